@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the TV-CT gradient-method path on GB300.
+
+One step = one GPBB solve and one UPN solve to the relative gradient-map
+norm eps, from x0 = 0, on the 64^3 few-view cone-beam problem (25 views,
+96 x 96 detector, 10 seeded ellipsoids, 1% noise, alpha 1e-2, tau 1e-4).
+Every part of the hot path runs inside a step: forward projection, back
+projection fused with the TV stencil, projected steps, the FP64 control
+reductions, BB / BT / mu-estimate control and the UPN extrapolation.
+
+value  = gradient evaluations (grad phi) per second inside the solves,
+         summed over ranks (independent problems per rank: weak scaling);
+e2e    = the same through the public call with host (pinned) b and x, the
+         copies inside the timed region;
+roofline = the dominant kernel (CSC back projection + TV, or CSR forward
+         projection) timed with CUDA events on its launch stream during the
+         timed region, algorithmic bytes per launch / mean duration.
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grad-phi evals/s and time-to-eps (GPBB/UPN) at 64^3, % of HBM roofline, vs plain FP32"
+UNIT = "grad-phi evals/s"
+WORKLOAD = ("TV-CT 64^3, cone beam 25 views x 96^2 px (Dso 192, Dod 128), 10 seeded ellipsoids, "
+            "1% noise, alpha 1e-2, tau 1e-4; one GPBB + one UPN solve to relative "
+            "gradient-map norm 1e-4 from x0 = 0")
+L2_NOTE = "inputs larger than L2: A stored as CSR + CSC (2 x 156 MB) > 129 MB L2"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c64")
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--graph", type=int, default=0,
+                    help="1: replay passes as CUDA graphs (no per-kernel timing)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phi-loop", type=int, default=200)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sms.sort()
+        med = sms[len(sms) // 2] if sms else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def make_problem(cfg, rank):
+    """Geometry, phantom and noise draw of this rank's problem (seeded inputs)."""
+    import synth
+    geom = cfg.geometry()
+    x_true = synth.ellipsoid_phantom(cfg.n, cfg.ellipsoids, cfg.semi_axes, cfg.values,
+                                     cfg.seed + 100 * rank)
+    z = synth.standard_normal(geom.m, cfg.seed + 1000 + 100 * rank)
+    return geom, x_true, z
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, cfg, eps):
+    """FP64 CPU oracle on the same workload; each step a bounded sample."""
+    import numpy as np
+    import oracle
+    geom, x_true, z = make_problem(cfg, 0)
+    A = oracle.system_matrix(geom)
+    b = oracle.make_data(A, x_true, z, cfg.noise)
+    prob = oracle.Problem(A=A, b=b, n=cfg.n, alpha=cfg.alpha, tau=cfg.tau)
+    x0 = np.zeros(prob.N)
+    k_sample = 3
+
+    def step():
+        g = 0
+        for fn in (oracle.solve_gpbb, oracle.solve_upn):
+            r = fn(prob, x0, eps, oracle.Options(k_max=k_sample))
+            g += r.g_evals
+        return g
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    evals = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = evals / dt
+    sample = (f"GPBB and UPN, first {k_sample} iterations each from x0 = 0 on the full 64^3 "
+              f"problem, per step ({evals} gradient evaluations in {dt:.1f} s)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": cfg.n, "nnz": int(A.nnz),
+                                        "parallelism": "single process, host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(cfg, eps, b_host, geom):
+    """The oracle as it stands on a bounded sample of the bench workload."""
+    import numpy as np
+    import oracle
+    A = oracle.system_matrix(geom)
+    prob = oracle.Problem(A=A, b=b_host.astype(np.float64), n=cfg.n, alpha=cfg.alpha, tau=cfg.tau)
+    x0 = np.zeros(prob.N)
+    k_sample = 8
+    t0 = time.perf_counter()
+    g = 0
+    for fn in (oracle.solve_gpbb, oracle.solve_upn):
+        g += fn(prob, x0, eps, oracle.Options(k_max=k_sample)).g_evals
+    dt = time.perf_counter() - t0
+    return {"value": g / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"GPBB and UPN, first {k_sample} iterations each on the same 64^3 problem "
+                      f"({g} gradient evaluations in {dt:.1f} s, FP64 numpy/scipy, one thread)"}
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    import synth
+    cfg = synth.get_config(args.config)
+    eps = args.eps if args.eps is not None else cfg.eps
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, cfg, eps)
+        return
+
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_1105_4002_gb300 as tvr
+
+    geom, x_true, z = make_problem(cfg, rank)
+    t0 = time.perf_counter()
+    sysm = tvr.System(geom)
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+
+    # data b = A x_true + e (forward projection on the GPU; noise from synth)
+    xt = torch.tensor(x_true, dtype=torch.float32, device=dev)
+    ax = torch.empty(geom.m, dtype=torch.float32, device=dev)
+    sysm.forward(xt, ax)
+    axh = ax.cpu().numpy().astype(np.float64)
+    sigma = cfg.noise * np.linalg.norm(axh) / math.sqrt(geom.m)
+    b_host = (axh + sigma * z).astype(np.float32)
+    b = torch.tensor(b_host, device=dev)
+    opts = tvr.SolveOptions(use_graph=bool(args.graph))
+
+    def step(bb, x_gp, x_up):
+        x_gp.zero_() if hasattr(x_gp, "zero_") else x_gp.fill(0)
+        x_up.zero_() if hasattr(x_up, "zero_") else x_up.fill(0)
+        r1 = sysm.solve("gpbb", bb, cfg.alpha, cfg.tau, eps, x_gp, opts)
+        r2 = sysm.solve("upn", bb, cfg.alpha, cfg.tau, eps, x_up, opts)
+        return r1, r2
+
+    xg = torch.zeros(geom.N, dtype=torch.float32, device=dev)
+    xu = torch.zeros(geom.N, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        step(b, xg, xu)
+    torch.cuda.synchronize()
+
+    # ---- timed region ----
+    sampler = ClockSampler(gpu_id_for(torch, dev))
+    if not args.graph:
+        sysm.profile(True)
+        sysm.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    evals = 0
+    passes = 0
+    launches = 0
+    t_gpbb, t_upn, it_gpbb, it_upn = [], [], [], []
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        r1 = sysm.solve("gpbb", b, cfg.alpha, cfg.tau, eps, xg.zero_(), opts)
+        s1 = time.perf_counter()
+        r2 = sysm.solve("upn", b, cfg.alpha, cfg.tau, eps, xu.zero_(), opts)
+        s2 = time.perf_counter()
+        t_gpbb.append(1e3 * (s1 - s0))
+        t_upn.append(1e3 * (s2 - s1))
+        it_gpbb.append(r1.iters)
+        it_upn.append(r2.iters)
+        evals += r1.g_evals + r2.g_evals
+        passes += r1.passes + r2.passes
+        # init (2) + per pass (3 GPBB / 4 UPN) + final phi (2)
+        launches += 2 + 3 * r1.passes + 2 + 2 + 4 * r2.passes + 2
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = sysm.profile_read() if not args.graph else None
+    sysm.profile(False)
+
+    tot = torch.tensor([float(evals), elapsed_ms], dtype=torch.float64, device=dev)
+    if dist:
+        ev_t = tot[:1].clone()
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+        t_t = tot[1:].clone()
+        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+        evals_all, elapsed_max = float(ev_t.item()), float(t_t.item())
+    else:
+        evals_all, elapsed_max = float(evals), elapsed_ms
+    value = evals_all / (elapsed_max / 1e3)
+
+    # ---- end-to-end through the public call with host buffers ----
+    b_pin = torch.tensor(b_host).pin_memory()
+    xg_h = torch.zeros(geom.N, dtype=torch.float32).pin_memory()
+    xu_h = torch.zeros(geom.N, dtype=torch.float32).pin_memory()
+    if dist:
+        dist.barrier()
+    e_evals = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r1 = sysm.solve("gpbb", b_pin, cfg.alpha, cfg.tau, eps, xg_h.zero_(), opts)
+        r2 = sysm.solve("upn", b_pin, cfg.alpha, cfg.tau, eps, xu_h.zero_(), opts)
+        e_evals += r1.g_evals + r2.g_evals
+    e_ms = 1e3 * (time.perf_counter() - t0)
+    e2e_value = e_evals / (e_ms / 1e3)
+    if dist:
+        tt = torch.tensor([float(e_evals), e_ms], dtype=torch.float64, device=dev)
+        a = tt[:1].clone()
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        m_ = tt[1:].clone()
+        dist.all_reduce(m_, op=dist.ReduceOp.MAX)
+        e2e_value = float(a.item()) / (float(m_.item()) / 1e3)
+
+    # ---- standalone phi_and_grad rate (same kernels, plain mode) ----
+    xr = torch.tensor(np.random.default_rng(rank).uniform(0, 1, geom.N), dtype=torch.float32,
+                      device=dev)
+    g = torch.empty(geom.N, dtype=torch.float32, device=dev)
+    phi_dev = torch.empty(4, dtype=torch.float64, device=dev)
+    for _ in range(5):
+        sysm.phi_and_grad(xr, b, cfg.alpha, cfg.tau, grad=g, phi_dev=phi_dev, sync=False)
+    sysm.profile(True)
+    sysm.profile_read()
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(args.phi_loop):
+        sysm.phi_and_grad(xr, b, cfg.alpha, cfg.tau, grad=g, phi_dev=phi_dev, sync=False)
+    p1.record()
+    torch.cuda.synchronize()
+    phi_prof = sysm.profile_read()
+    sysm.profile(False)
+    phi_ms = p0.elapsed_time(p1) / args.phi_loop
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    m, N, nnz = geom.m, geom.N, sysm.nnz
+    # algorithmic bytes per launch (solver mode; float32 values, int32 indices, int64 pointers)
+    bytes_bwd = 8 * nnz + 8 * (N + 1) + 4 * m + 3 * 4 * N     # A^T, r gather, x stencil, g, (x_prev|x+)
+    bytes_fwd = 8 * nnz + 8 * (m + 1) + 2 * 4 * N + 3 * 4 * m  # A, trial + base gathers, b, r, Ad
+    peak, peak_kind = measured_peak_gbs()
+    roof = None
+    if prof:
+        (nf, msf), (nb, msb) = prof["forward"], prof["backward"]
+        cands = []
+        if nb:
+            cands.append(("bwd_csc_tv", msb, nb, bytes_bwd))
+        if nf:
+            cands.append(("fwd_csr_trial", msf, nf, bytes_fwd))
+        name, ms, cnt, by = max(cands, key=lambda c: c[1])
+        avg_s = ms / cnt / 1e3
+        ach = by / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": name, "launches": cnt, "avg_us": 1e6 * avg_s,
+                "algorithmic_bytes_per_launch": by, "peak_source": peak_kind,
+                "share_of_timed_region": ms / elapsed_ms,
+                "other": {"fwd_us": 1e3 * msf / max(nf, 1), "bwd_us": 1e3 * msb / max(nb, 1),
+                          "fwd_frac": bytes_fwd / (msf / max(nf, 1) / 1e3) / 1e9 / peak if nf else None,
+                          "bwd_frac": bytes_bwd / (msb / max(nb, 1) / 1e3) / 1e9 / peak if nb else None}}
+    pf, pb = phi_prof["forward"], phi_prof["backward"]
+    plain_f = 8 * nnz + 8 * (m + 1) + 4 * N + 8 * m
+    plain_b = 8 * nnz + 8 * (N + 1) + 4 * m + 8 * N
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": cfg.n, "views": cfg.views, "det": cfg.det,
+                   "m": m, "N": N, "nnz": nnz, "alpha": cfg.alpha, "tau": cfg.tau, "eps": eps,
+                   "stop": "relative gradient-map norm", "methods": ["gpbb", "upn"],
+                   "l2": L2_NOTE, "passes_as_graphs": bool(args.graph),
+                   "parallelism": f"{world} independent problems (one per GPU)"},
+        "time_to_eps": {"gpbb_ms": sorted(t_gpbb)[len(t_gpbb) // 2],
+                        "upn_ms": sorted(t_upn)[len(t_upn) // 2],
+                        "gpbb_iters": it_gpbb[-1], "upn_iters": it_upn[-1],
+                        "build_system_ms": build_ms},
+        "phi_and_grad": {"evals_per_s": 1e3 / phi_ms, "us_per_eval": 1e3 * phi_ms,
+                         "fwd_us": 1e3 * pf[1] / max(pf[0], 1), "bwd_us": 1e3 * pb[1] / max(pb[0], 1),
+                         "fwd_frac": plain_f / (pf[1] / max(pf[0], 1) / 1e3) / 1e9 / peak if pf[0] else None,
+                         "bwd_frac": plain_b / (pb[1] / max(pb[0], 1) / 1e3) / 1e9 / peak if pb[0] else None},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * 4 * (m + N), "d2h_bytes_per_step": 2 * 4 * N},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, eps, b_host, geom)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

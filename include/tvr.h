@@ -1,0 +1,241 @@
+/*
+ * tvr.h -- C ABI of the GB300 TV-CT gradient-method library (libtvr.so).
+ *
+ * Problem (Sec. II-A, eq. TVobjectivefunction, eq. TV):
+ *     x* = argmin_{x in Q} phi(x),  phi(x) = 1/2 ||A x - b||_2^2 + alpha TV_tau(x),
+ *     Q = R_+^N (Sec. IV-A),
+ * where A is the ray-voxel system matrix (Siddon intersection lengths) and
+ * TV_tau(x) = sum_j h_tau(D_j x) is the Huber-smoothed discrete TV with
+ * forward differences D_j (h_tau(z) = ||z|| - tau/2 for ||z|| >= tau,
+ * ||z||^2 / (2 tau) otherwise; a difference leaving the grid is 0).
+ *
+ * Conventions shared by every call:
+ *   - volume: n x n x n unit voxels centred at the origin; voxel
+ *     j = ix + n*iy + n*n*iz (x fastest); N = n^3;
+ *   - rays: view v, detector pixel (p, q) -> row i = v*Pu*Pv + q*Pu + p;
+ *     m = V*Pu*Pv;
+ *   - vectors are float32, contiguous; x, grad: N entries; b, resid: m.
+ *   - "host or device": a vector argument may point to device memory or to
+ *     host memory (pageable or pinned); host vectors are staged through
+ *     device buffers owned by the system, with the copies on `stream`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is asynchronous on `stream` unless a call says that it
+ *     synchronises.  Calls that use one tvr_system share its workspace and
+ *     must be ordered on one stream (or otherwise serialised by the caller).
+ *   - Return value: a tvr_status; no exception crosses the ABI.
+ *     tvr_last_error() gives a message for the calling thread's last error.
+ */
+#ifndef TVR_H
+#define TVR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TVR_API __attribute__((visibility("default")))
+#else
+#define TVR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tvr_status {
+  TVR_OK = 0,
+  TVR_NOT_CONVERGED = 1,   /* warning: stopped at k_max */
+  TVR_ERR_ARG = -1,        /* invalid argument; nothing was launched */
+  TVR_ERR_OOM = -2,        /* a device allocation failed */
+  TVR_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+  TVR_ERR_LINESEARCH = -4, /* a line search hit its trial cap */
+  TVR_ERR_NONFINITE = -5   /* a control scalar became NaN or Inf */
+} tvr_status;
+
+typedef enum tvr_geometry_kind {
+  TVR_CONE = 0,     /* every ray of a view starts at the view's point source */
+  TVR_PARALLEL = 1  /* ray of pixel (p, q) starts at src + pixel offset */
+} tvr_geometry_kind;
+
+typedef enum tvr_storage {
+  TVR_STORAGE_FP32 = 0 /* CSR and CSC, float32 values, int32 indices, int64 pointers */
+} tvr_storage;
+
+/* Number of doubles per view record. */
+#define TVR_VIEW_FIELDS 12
+
+/*
+ * Scan geometry.  `views` is a HOST array of n_views records of 12 doubles:
+ * source (or source-plane centre for TVR_PARALLEL) [3], detector centre [3],
+ * detector column step u [3] and row step w [3] (pixel pitch included).
+ * Pixel (p, q) has centre det + (p - (Pu-1)/2) u + (q - (Pv-1)/2) w.
+ */
+typedef struct tvr_geometry {
+  int32_t n;         /* grid edge, >= 1 */
+  int32_t n_views;   /* V >= 1 */
+  int32_t det_cols;  /* Pu >= 1 */
+  int32_t det_rows;  /* Pv >= 1 */
+  int32_t kind;      /* tvr_geometry_kind */
+  int32_t reserved;  /* must be 0 */
+  const double *views;
+} tvr_geometry;
+
+typedef struct tvr_system tvr_system; /* opaque; owns A and all workspace */
+
+/*
+ * Build A for a geometry (Sec. II-A: A maps the image to ray sums; its entries
+ * here are Siddon ray-voxel intersection lengths computed in FP64 and stored in
+ * FP32): each ray is clipped to the volume box, the crossing parameters of all
+ * grid planes are merged in increasing order (equal values once), and each
+ * consecutive pair gives one entry (voxel of the midpoint, length (t_b - t_a)|d|).
+ * Stores CSR (rows in traversal order) and its transpose CSC (rows ascending
+ * within a column).  Synchronises `stream` once (to size the arrays).
+ * *out receives a new system owned by the caller, freed by tvr_system_free.
+ * Errors: TVR_ERR_ARG (bad geometry, n^3 >= 2^31), TVR_ERR_OOM, TVR_ERR_CUDA.
+ */
+TVR_API int tvr_build_system(const tvr_geometry *geom, int32_t storage, void *stream,
+                     tvr_system **out);
+
+/* Free a system and every device buffer it owns (synchronises the device). */
+TVR_API int tvr_system_free(tvr_system *sys);
+
+/* Shape of A: m rows (rays), N columns (voxels), nnz stored entries (host outputs, nullable). */
+TVR_API int tvr_system_shape(const tvr_system *sys, int64_t *m, int64_t *N, int64_t *nnz);
+
+/*
+ * Copy A to caller-owned HOST buffers (synchronous): CSR row_ptr[m+1],
+ * col[nnz], val[nnz]; CSC col_ptr[N+1], row[nnz], val[nnz].  Any pointer may be
+ * NULL to skip that array.
+ */
+TVR_API int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col, float *val);
+TVR_API int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val);
+
+/* y = A x (forward projection).  x: N, y: m; host or device. */
+TVR_API int tvr_forward(const tvr_system *sys, const float *x, float *y, void *stream);
+
+/* z = A^T r (back projection, atomic-free CSC gather).  r: m, z: N; host or device. */
+TVR_API int tvr_adjoint(const tvr_system *sys, const float *r, float *z, void *stream);
+
+/*
+ * phi and its gradient (eq. TVobjectivefunction):
+ *   resid = A x - b,  phi = 1/2 ||resid||^2 + alpha TV_tau(x),
+ *   grad  = A^T resid + alpha grad TV_tau(x),
+ *   grad TV_tau(x) = sum_j D_j^T (D_j x / max(tau, ||D_j x||)).
+ * x: N, b: m (host or device).  grad (N) and resid (m) are nullable outputs,
+ * host or device; grad == NULL evaluates phi only (no back projection).
+ * phi_dev: nullable DEVICE array of 3 doubles {phi, 1/2||r||^2, TV_tau(x)};
+ * phi_host: nullable HOST array of 3 doubles, same content -- giving it
+ * synchronises `stream`.  The reductions accumulate in double-single (~48-bit)
+ * arithmetic and are delivered in FP64; results are deterministic.
+ * alpha >= 0, tau > 0 (TVR_ERR_ARG otherwise).
+ */
+TVR_API int tvr_phi_and_grad(const tvr_system *sys, const float *x, const float *b, double alpha,
+                     double tau, double *phi_dev, double *phi_host, float *grad,
+                     float *resid, void *stream);
+
+/* In place x <- P_Q(x) = max(x, 0) on n DEVICE floats (Sec. III-A); NaN stays NaN. */
+TVR_API int tvr_project_Q(float *x, int64_t n, void *stream);
+
+/*
+ * ||G_nu(x)||_2 with G_nu(x) = nu (x - P_Q(x - grad / nu)) (Sec. III-D) for
+ * DEVICE vectors x, grad of N floats (N of `sys`, whose workspace is used);
+ * the FP64 result is written to the HOST double *out (synchronises `stream`).
+ * nu > 0 and finite.
+ */
+TVR_API int tvr_gradient_map_norm(const tvr_system *sys, const float *x, const float *grad, double nu,
+                          double *out, void *stream);
+
+/* Stopping normalisation of the gradient-map test (Sec. III-D). */
+typedef enum tvr_stop_mode {
+  TVR_STOP_REL = 0,   /* ||G_k|| / ||G_0|| <= eps (G_0: gradient map of iteration 0) */
+  TVR_STOP_PER_N = 1  /* ||G_k|| / N <= eps, as printed in the paper */
+} tvr_stop_mode;
+
+/* Number of doubles per history record: k, ||G||, L or theta, mu, beta, trials, f, stop value. */
+#define TVR_HIST_FIELDS 8
+
+typedef struct tvr_solve_opts {
+  int32_t k_max;            /* iteration cap (default 20000) -> TVR_NOT_CONVERGED */
+  int32_t stop_mode;        /* tvr_stop_mode (default TVR_STOP_REL) */
+  int32_t gpbb_K;           /* GPBB memory K (default 2, Sec. III-A), 0..8 */
+  int32_t gpbb_max_trials;  /* squarings of beta per GPBB iteration (default 12) */
+  int32_t bt_max;           /* increases of L per BT call (default 60) */
+  int32_t use_graph;        /* 1 (default): batches of passes replayed as CUDA graphs */
+  int32_t batch;            /* passes launched between host checks (default 32) */
+  int32_t reserved;
+  double gpbb_sigma;        /* default 0.1 (Sec. III-A) */
+  double gpbb_beta0;        /* default 0.95 (Alg. 1) */
+  double rho_L;             /* BT factor (Alg. 2), default 2 */
+  double L_bar;             /* initial L estimate (Alg. 2 / Alg. 3), default 1 */
+  double mu_bar;            /* initial mu (Alg. 3), default 0.1 * L_bar */
+  double *history;          /* nullable HOST array [history_len * TVR_HIST_FIELDS] */
+  int64_t history_len;      /* records available in history */
+} tvr_solve_opts;
+
+typedef struct tvr_solve_info {
+  int32_t status;       /* tvr_status of the solve */
+  int32_t iters;        /* accepted iterations (GP/GPBB: k+1; UPN: BT calls) */
+  int32_t f_evals;      /* objective evaluations (forward projections of trial points) */
+  int32_t g_evals;      /* gradient evaluations (back projections) */
+  int32_t trials;       /* rejected line-search / BT trials in total */
+  int32_t passes;       /* passes launched, including no-op passes after the stop */
+  int32_t history_used; /* records written to opts->history */
+  int32_t reserved;
+  double phi;           /* phi(x*) evaluated afresh at the returned point */
+  double gnorm;         /* ||G|| of the last iteration */
+  double gnorm0;        /* ||G|| of iteration 0 */
+  double stop_value;    /* the tested quantity of the last iteration */
+  double L;             /* GP/UPN: last L_k; GPBB: 1/theta */
+  double theta;         /* GPBB: last BB step; UPN: last theta_k */
+  double mu;            /* UPN: last mu_k */
+} tvr_solve_info;
+
+/* Fill *opts with the defaults listed above. */
+TVR_API void tvr_solve_opts_default(tvr_solve_opts *opts);
+
+/*
+ * Solvers.  x holds x^(0) on entry (host or device; N floats) and the result on
+ * return.  b: m floats, host or device.  eps > 0.  opts nullable (defaults).
+ * info nullable (host).  These calls synchronise `stream`.
+ *
+ * tvr_solve_gp   -- eq. (gradientmethod), x+ = P_Q(x - theta_k grad phi(x)) with
+ *                   theta_k = 1/L_k from BT (Alg. 2) started at L_{k-1}; stop on
+ *                   ||G_{L_k}(x^(k))||.
+ * tvr_solve_gpbb -- Alg. 1: Barzilai-Borwein theta_k, beta from 0.95 squared until
+ *                   f(xbar) < max_{i<=K} f(x^(k-i)) - sigma grad f^T (x - xbar);
+ *                   stop on ||G_{1/theta_k}(x^(k))||.
+ * tvr_solve_upn  -- Alg. 3: BT from y^(k), mu_k = min(mu_{k-1}, M(x^(k), y^(k)))
+ *                   (eq. mu_k_estimate), theta_{k+1} the positive root of
+ *                   theta^2 = (1 - theta) theta_k^2 + (mu_k / L_k) theta,
+ *                   beta_k = theta_k (1 - theta_k) / (theta_k^2 + theta_{k+1}),
+ *                   y^(k+1) = x^(k+1) + beta_k (x^(k+1) - x^(k)); stop on
+ *                   ||G_{L_k}(y^(k))||.
+ * Returns the solve status (also in info->status).
+ */
+TVR_API int tvr_solve_gp(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                 const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream);
+TVR_API int tvr_solve_gpbb(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                   const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream);
+TVR_API int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                  const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream);
+
+/*
+ * Kernel timing for measurement: while enabled, the library records a CUDA
+ * event pair on the launch stream around every forward (CSR) and back (CSC +
+ * TV) projection kernel launched outside a CUDA graph.  tvr_profile_read
+ * synchronises those events and returns, per kernel kind (0 = forward,
+ * 1 = back projection), the number of timed launches and their total time in
+ * milliseconds (host outputs), then resets the counters.
+ */
+TVR_API int tvr_profile_enable(tvr_system *sys, int32_t enable);
+TVR_API int tvr_profile_read(tvr_system *sys, int64_t counts[2], double total_ms[2]);
+
+/* Name of a status code. */
+TVR_API const char *tvr_status_str(int status);
+
+/* Message describing the calling thread's most recent error (never NULL). */
+TVR_API const char *tvr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TVR_H */

@@ -1,0 +1,363 @@
+// C ABI of libtvr (declared in include/tvr.h): system ownership, argument
+// checks, host/device staging, and the solver pass loop.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tvr_internal.cuh"
+
+#include "system.cuh"
+
+thread_local std::string g_last_error = "no error";
+
+int tvr_fail(int status, const std::string &msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int tvr_cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TVR_ERR_OOM : TVR_ERR_CUDA;
+}
+
+extern "C" {
+
+const char *tvr_status_str(int status) {
+  switch (status) {
+    case TVR_OK: return "TVR_OK";
+    case TVR_NOT_CONVERGED: return "TVR_NOT_CONVERGED";
+    case TVR_ERR_ARG: return "TVR_ERR_ARG";
+    case TVR_ERR_OOM: return "TVR_ERR_OOM";
+    case TVR_ERR_CUDA: return "TVR_ERR_CUDA";
+    case TVR_ERR_LINESEARCH: return "TVR_ERR_LINESEARCH";
+    case TVR_ERR_NONFINITE: return "TVR_ERR_NONFINITE";
+    default: return "TVR_UNKNOWN_STATUS";
+  }
+}
+
+const char *tvr_last_error(void) { return g_last_error.c_str(); }
+
+int tvr_system_free(tvr_system *sys) {
+  if (!sys) return TVR_OK;
+  cudaSetDevice(sys->device);
+  cudaDeviceSynchronize();
+  for (auto &g : sys->pass_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < kProfPairs; ++i)
+      for (int w = 0; w < 2; ++w)
+        if (sys->prof_ev[k][i][w]) cudaEventDestroy(sys->prof_ev[k][i][w]);
+  void *ptrs[] = {sys->row_ptr, sys->col_ptr, sys->col, sys->row, sys->val, sys->cval,
+                  sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
+                  sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (float *p : sys->vN)
+    if (p) cudaFree(p);
+  for (float *p : sys->vM)
+    if (p) cudaFree(p);
+  if (sys->pinned_flag) cudaFreeHost(sys->pinned_flag);
+  if (sys->prof_flags_host) cudaFreeHost(sys->prof_flags_host);
+  delete sys;
+  return TVR_OK;
+}
+
+int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_system **out) {
+  if (!g || !out) return fail(TVR_ERR_ARG, "tvr_build_system: null argument");
+  *out = nullptr;
+  if (storage != TVR_STORAGE_FP32) return fail(TVR_ERR_ARG, "tvr_build_system: unknown storage");
+  if (g->n < 1 || g->n_views < 1 || g->det_cols < 1 || g->det_rows < 1 || !g->views ||
+      (g->kind != TVR_CONE && g->kind != TVR_PARALLEL) || g->reserved != 0)
+    return fail(TVR_ERR_ARG, "tvr_build_system: invalid geometry");
+  const int64_t N = (int64_t)g->n * g->n * g->n;
+  if (N >= (int64_t)1 << 31 || g->n > 1 << 20)
+    return fail(TVR_ERR_ARG, "tvr_build_system: n^3 must be < 2^31");
+  for (int64_t i = 0; i < (int64_t)g->n_views * TVR_VIEW_FIELDS; ++i)
+    if (!std::isfinite(g->views[i])) return fail(TVR_ERR_ARG, "tvr_build_system: non-finite view");
+  cudaStream_t s = (cudaStream_t)stream;
+  tvr_system *sys = new tvr_system();
+  int rc = TVR_OK;
+  double *views_dev = nullptr;
+  int64_t *counts = nullptr, *tmp = nullptr, *key = nullptr, *ccnt = nullptr;
+  auto cleanup = [&]() {
+    if (views_dev) cudaFree(views_dev);
+    if (counts) cudaFree(counts);
+    if (tmp) cudaFree(tmp);
+    if (key) cudaFree(key);
+    if (ccnt) cudaFree(ccnt);
+  };
+#define BUILD_CUDA(call)                          \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) {                      \
+      rc = cuda_fail(e_, #call);                  \
+      cleanup();                                  \
+      tvr_system_free(sys);                       \
+      return rc;                                  \
+    }                                             \
+  } while (0)
+  BUILD_CUDA(cudaGetDevice(&sys->device));
+  sys->n = g->n;
+  sys->V = g->n_views;
+  sys->Pu = g->det_cols;
+  sys->Pv = g->det_rows;
+  sys->kind = g->kind;
+  sys->m = (int64_t)g->n_views * g->det_cols * g->det_rows;
+  sys->N = N;
+  const int64_t m = sys->m;
+  const size_t vbytes = sizeof(double) * TVR_VIEW_FIELDS * g->n_views;
+  BUILD_CUDA(cudaMalloc(&views_dev, vbytes));
+  BUILD_CUDA(cudaMemcpyAsync(views_dev, g->views, vbytes, cudaMemcpyHostToDevice, s));
+  BUILD_CUDA(cudaMalloc(&counts, sizeof(int64_t) * m));
+  const int64_t tl = scan_tmp_len(m > N ? m : N);
+  BUILD_CUDA(cudaMalloc(&tmp, sizeof(int64_t) * tl));
+  BUILD_CUDA(cudaMalloc(&sys->row_ptr, sizeof(int64_t) * (m + 1)));
+  BUILD_CUDA(siddon_count(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, counts, s));
+  BUILD_CUDA(scan_exclusive_i64(counts, m, sys->row_ptr, tmp, s));
+  int64_t nnz = 0;
+  BUILD_CUDA(cudaMemcpyAsync(&nnz, sys->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BUILD_CUDA(cudaStreamSynchronize(s));
+  sys->nnz = nnz;
+  const int64_t nz1 = nnz > 0 ? nnz : 1;
+  BUILD_CUDA(cudaMalloc(&sys->col, sizeof(int32_t) * nz1));
+  BUILD_CUDA(cudaMalloc(&sys->val, sizeof(float) * nz1));
+  BUILD_CUDA(siddon_fill(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, sys->row_ptr,
+                         sys->col, sys->val, s));
+  BUILD_CUDA(cudaMalloc(&sys->col_ptr, sizeof(int64_t) * (N + 1)));
+  BUILD_CUDA(cudaMalloc(&sys->row, sizeof(int32_t) * nz1));
+  BUILD_CUDA(cudaMalloc(&sys->cval, sizeof(float) * nz1));
+  BUILD_CUDA(cudaMalloc(&key, sizeof(int64_t) * nz1));
+  BUILD_CUDA(cudaMalloc(&ccnt, sizeof(int64_t) * N));
+  BUILD_CUDA(csr_to_csc(sys->row_ptr, sys->col, sys->val, m, N, nnz, sys->col_ptr, sys->row,
+                        sys->cval, ccnt, key, tmp, s));
+  // reduction workspace: per slot partials + counter + outputs
+  const size_t part = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;
+  const size_t slot_bytes = part + 256 + 256;
+  BUILD_CUDA(cudaMalloc(&sys->ws_mem, slot_bytes * kSlots));
+  BUILD_CUDA(cudaMemsetAsync(sys->ws_mem, 0, slot_bytes * kSlots, s));
+  RedSlot *slots[kSlots] = {&sys->ws.fwd, &sys->ws.bwd, &sys->ws.step,
+                            &sys->ws.yf,  &sys->ws.tv,  &sys->ws.gmap};
+  for (int k = 0; k < kSlots; ++k) {
+    char *b = (char *)sys->ws_mem + slot_bytes * k;
+    slots[k]->partials = (FF *)b;
+    slots[k]->counter = (unsigned *)(b + part);
+    slots[k]->out = (double *)(b + part + 256);
+  }
+  kernel_grids(sys->ws, sys->device);
+  BUILD_CUDA(cudaMalloc(&sys->phi_ws, sizeof(double) * 4));
+  BUILD_CUDA(cudaStreamSynchronize(s));
+  BUILD_CUDA(cudaGetLastError());
+#undef BUILD_CUDA
+  cleanup();
+  *out = sys;
+  return TVR_OK;
+}
+
+int tvr_system_shape(const tvr_system *sys, int64_t *m, int64_t *N, int64_t *nnz) {
+  if (!sys) return fail(TVR_ERR_ARG, "tvr_system_shape: null system");
+  if (m) *m = sys->m;
+  if (N) *N = sys->N;
+  if (nnz) *nnz = sys->nnz;
+  return TVR_OK;
+}
+
+int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col, float *val) {
+  if (!sys) return fail(TVR_ERR_ARG, "export: null system");
+  TVR_CUDA(cudaSetDevice(sys->device));
+  TVR_CUDA(cudaDeviceSynchronize());
+  if (row_ptr)
+    TVR_CUDA(cudaMemcpy(row_ptr, sys->row_ptr, sizeof(int64_t) * (sys->m + 1), cudaMemcpyDeviceToHost));
+  if (col && sys->nnz)
+    TVR_CUDA(cudaMemcpy(col, sys->col, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
+  if (val && sys->nnz)
+    TVR_CUDA(cudaMemcpy(val, sys->val, sizeof(float) * sys->nnz, cudaMemcpyDeviceToHost));
+  return TVR_OK;
+}
+
+int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val) {
+  if (!sys) return fail(TVR_ERR_ARG, "export: null system");
+  TVR_CUDA(cudaSetDevice(sys->device));
+  TVR_CUDA(cudaDeviceSynchronize());
+  if (col_ptr)
+    TVR_CUDA(cudaMemcpy(col_ptr, sys->col_ptr, sizeof(int64_t) * (sys->N + 1), cudaMemcpyDeviceToHost));
+  if (row && sys->nnz)
+    TVR_CUDA(cudaMemcpy(row, sys->row, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
+  if (val && sys->nnz)
+    TVR_CUDA(cudaMemcpy(val, sys->cval, sizeof(float) * sys->nnz, cudaMemcpyDeviceToHost));
+  return TVR_OK;
+}
+
+int tvr_forward(const tvr_system *csys, const float *x, float *y, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !y) return fail(TVR_ERR_ARG, "tvr_forward: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float *xd;
+  int rc = stage_in(x, sys->N, &sys->stage_xN, s, &xd);
+  if (rc) return rc;
+  const bool yh = !is_device_ptr(y);
+  float *yd = y;
+  if (yh) {
+    if ((rc = ensure_vec(&sys->stage_rM, sys->m))) return rc;
+    yd = sys->stage_rM;
+  }
+  prof_mark(sys, 0, 0, s);
+  launch_forward_plain(sys->mat(), xd, yd, sys->ws, s);
+  prof_mark(sys, 0, 1, s);
+  TVR_CUDA(cudaGetLastError());
+  if (yh) {
+    TVR_CUDA(cudaMemcpyAsync(y, yd, sizeof(float) * sys->m, cudaMemcpyDeviceToHost, s));
+    TVR_CUDA(cudaStreamSynchronize(s));
+  }
+  return TVR_OK;
+}
+
+int tvr_adjoint(const tvr_system *csys, const float *r, float *z, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !r || !z) return fail(TVR_ERR_ARG, "tvr_adjoint: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float *rd;
+  int rc = stage_in(r, sys->m, &sys->stage_bM, s, &rd);
+  if (rc) return rc;
+  const bool zh = !is_device_ptr(z);
+  float *zd = z;
+  if (zh) {
+    if ((rc = ensure_vec(&sys->stage_gN, sys->N))) return rc;
+    zd = sys->stage_gN;
+  }
+  prof_mark(sys, 1, 0, s);
+  launch_adjoint_plain(sys->mat(), rd, zd, sys->ws, s);
+  prof_mark(sys, 1, 1, s);
+  TVR_CUDA(cudaGetLastError());
+  if (zh) {
+    TVR_CUDA(cudaMemcpyAsync(z, zd, sizeof(float) * sys->N, cudaMemcpyDeviceToHost, s));
+    TVR_CUDA(cudaStreamSynchronize(s));
+  }
+  return TVR_OK;
+}
+
+int tvr_phi_and_grad(const tvr_system *csys, const float *x, const float *b, double alpha, double tau,
+                     double *phi_dev, double *phi_host, float *grad, float *resid, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !b) return fail(TVR_ERR_ARG, "tvr_phi_and_grad: null argument");
+  if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
+    return fail(TVR_ERR_ARG, "tvr_phi_and_grad: need alpha >= 0 and tau > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  const float *xd, *bd;
+  if ((rc = stage_in(x, sys->N, &sys->stage_xN, s, &xd))) return rc;
+  if ((rc = stage_in(b, sys->m, &sys->stage_bM, s, &bd))) return rc;
+  bool sync = phi_host != nullptr;
+  float *rd = resid;
+  const bool rh = resid && !is_device_ptr(resid);
+  if (!resid || rh) {
+    if ((rc = ensure_vec(&sys->stage_rM, sys->m))) return rc;
+    rd = sys->stage_rM;
+  }
+  double *pd = phi_dev ? phi_dev : sys->phi_ws;
+  const MatDev A = sys->mat();
+  prof_mark(sys, 0, 0, s);
+  launch_forward(A, xd, bd, rd, sys->ws, s);
+  prof_mark(sys, 0, 1, s);
+  if (grad) {
+    const bool gh = !is_device_ptr(grad);
+    float *gd = grad;
+    if (gh) {
+      if ((rc = ensure_vec(&sys->stage_gN, sys->N))) return rc;
+      gd = sys->stage_gN;
+    }
+    prof_mark(sys, 1, 0, s);
+    launch_backward(A, rd, xd, (float)alpha, (float)tau, gd, sys->ws, pd, s);
+    prof_mark(sys, 1, 1, s);
+    if (gh) {
+      TVR_CUDA(cudaMemcpyAsync(grad, gd, sizeof(float) * sys->N, cudaMemcpyDeviceToHost, s));
+      sync = true;
+    }
+  } else {
+    launch_tv_value(A, xd, (float)alpha, (float)tau, sys->ws, pd, s);
+  }
+  TVR_CUDA(cudaGetLastError());
+  if (rh) {
+    TVR_CUDA(cudaMemcpyAsync(resid, rd, sizeof(float) * sys->m, cudaMemcpyDeviceToHost, s));
+    sync = true;
+  }
+  if (phi_host) TVR_CUDA(cudaMemcpyAsync(phi_host, pd, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  if (sync) TVR_CUDA(cudaStreamSynchronize(s));
+  return TVR_OK;
+}
+
+int tvr_project_Q(float *x, int64_t n, void *stream) {
+  if (n < 0 || (!x && n > 0)) return fail(TVR_ERR_ARG, "tvr_project_Q: bad arguments");
+  if (n == 0) return TVR_OK;
+  if (!is_device_ptr(x)) return fail(TVR_ERR_ARG, "tvr_project_Q: x must be device memory");
+  launch_project(x, n, (cudaStream_t)stream);
+  TVR_CUDA(cudaGetLastError());
+  return TVR_OK;
+}
+
+void tvr_solve_opts_default(tvr_solve_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->k_max = 20000;
+  o->stop_mode = TVR_STOP_REL;
+  o->gpbb_K = 2;
+  o->gpbb_max_trials = 12;
+  o->bt_max = 60;
+  o->use_graph = 1;
+  o->batch = 32;
+  o->gpbb_sigma = 0.1;
+  o->gpbb_beta0 = 0.95;
+  o->rho_L = 2.0;
+  o->L_bar = 1.0;
+  o->mu_bar = 0.1;
+}
+
+int tvr_profile_enable(tvr_system *sys, int32_t enable) {
+  if (!sys) return fail(TVR_ERR_ARG, "tvr_profile_enable: null system");
+  if (enable && !sys->prof_ev[0][0][0]) {
+    for (int k = 0; k < 2; ++k)
+      for (int i = 0; i < kProfPairs; ++i)
+        for (int w = 0; w < 2; ++w) TVR_CUDA(cudaEventCreate(&sys->prof_ev[k][i][w]));
+    TVR_CUDA(cudaMalloc(&sys->prof_flags_dev, sizeof(int) * 2 * kProfPairs));
+    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * 2 * kProfPairs));
+    TVR_CUDA(cudaMallocHost(&sys->prof_flags_host, sizeof(int) * 2 * kProfPairs));
+  }
+  if (!enable && sys->profile)
+    if (int rc = prof_harvest(sys)) return rc;
+  sys->profile = enable ? 1 : 0;
+  return TVR_OK;
+}
+
+int tvr_profile_read(tvr_system *sys, int64_t counts[2], double total_ms[2]) {
+  if (!sys || !counts || !total_ms) return fail(TVR_ERR_ARG, "tvr_profile_read: null argument");
+  if (int rc = prof_harvest(sys)) return rc;
+  for (int k = 0; k < 2; ++k) {
+    counts[k] = sys->prof_cnt[k];
+    total_ms[k] = sys->prof_ms[k];
+    sys->prof_cnt[k] = 0;
+    sys->prof_ms[k] = 0.0;
+  }
+  return TVR_OK;
+}
+
+}  // extern "C"
+
+extern "C" int tvr_gradient_map_norm(const tvr_system *csys, const float *x, const float *grad,
+                                     double nu, double *out, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !grad || !out || !(nu > 0.0) || !std::isfinite(nu))
+    return fail(TVR_ERR_ARG, "tvr_gradient_map_norm: bad arguments");
+  if (!is_device_ptr(x) || !is_device_ptr(grad))
+    return fail(TVR_ERR_ARG, "tvr_gradient_map_norm: x and grad must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_gmap_norm(x, grad, sys->N, nu, sys->ws, s);
+  TVR_CUDA(cudaGetLastError());
+  TVR_CUDA(cudaMemcpyAsync(out, sys->ws.gmap.out + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TVR_CUDA(cudaStreamSynchronize(s));
+  return TVR_OK;
+}

@@ -1,0 +1,333 @@
+// Construction of A (Siddon ray-voxel lengths) and of its transpose.
+//
+// One thread traces one ray in FP64.  Every FP64 product, sum, quotient and
+// square root is written with an explicit round-to-nearest intrinsic, so the
+// compiler cannot fuse or reorder them: the traversal is a fixed sequence of
+// correctly rounded IEEE operations, and the index sets do not depend on the
+// compiler's contraction choices.
+//
+// Traversal (Sec. II-A defines A only as the ray-sum operator; the entries
+// are the lengths of ray i inside voxel j):
+//   d = c - s for source s and pixel centre c; the ray is clipped to the box
+//   [-n/2, n/2]^3 by t_min / t_max; the parameters of all grid planes strictly
+//   between them are merged in increasing order with equal values once; each
+//   consecutive pair (t_a, t_b) is one entry: voxel floor(s + (t_a+t_b)/2 d + n/2)
+//   per axis (clamped to [0, n-1]), length (t_b - t_a) |d|, stored as float32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tvr_internal.cuh"
+
+namespace {
+
+struct ViewRec {
+  double v[TVR_VIEW_FIELDS];
+};
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// Ray endpoints of pixel (p, q): centre c = (det + a u) + b w; for parallel
+// beam the start s = (src + a u) + b w, else s = src.
+__device__ __forceinline__ void endpoints(const double *vw, int kind, int Pu, int Pv, int p, int q,
+                                          double s[3], double c[3]) {
+  const double a = dsub((double)p, dmul(0.5, (double)(Pu - 1)));
+  const double b = dsub((double)q, dmul(0.5, (double)(Pv - 1)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double au = dmul(a, vw[6 + k]);
+    const double bw = dmul(b, vw[9 + k]);
+    c[k] = dadd(dadd(vw[3 + k], au), bw);
+    s[k] = kind == TVR_PARALLEL ? dadd(dadd(vw[k], au), bw) : vw[k];
+  }
+}
+
+__device__ __forceinline__ double plane_param(int i, double half, double s, double d) {
+  return ddiv(dsub(dsub((double)i, half), s), d);
+}
+
+// Returns the number of entries of the ray; writes them when cols != nullptr.
+template <bool FILL>
+__device__ int trace(const double s[3], const double c[3], int n, int32_t *cols, float *vals) {
+  const double half = dmul(0.5, (double)n);
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = dsub(c[k], s[k]);
+  const double dnorm =
+      __dsqrt_rn(dadd(dadd(dmul(d[0], d[0]), dmul(d[1], d[1])), dmul(d[2], d[2])));
+  double tmin = 0.0, tmax = 1.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] != 0.0) {
+      const double t0 = ddiv(dsub(-half, s[k]), d[k]);
+      const double t1 = ddiv(dsub(half, s[k]), d[k]);
+      const double lo = t0 < t1 ? t0 : t1;
+      const double hi = t0 < t1 ? t1 : t0;
+      if (lo > tmin) tmin = lo;
+      if (hi < tmax) tmax = hi;
+    } else if (!(s[k] > -half && s[k] < half)) {
+      return 0;
+    }
+  }
+  if (!(tmax > tmin)) return 0;
+
+  int idx[3] = {0, 0, 0}, dir[3] = {0, 0, 0};
+  bool act[3] = {false, false, false};
+  double tn[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] == 0.0) continue;
+    dir[k] = d[k] > 0.0 ? 1 : -1;
+    // first plane index at or before the entry point (only a starting guess:
+    // the skip loop below decides exactly which planes lie beyond t_min)
+    const int i0 = (int)floor(dadd(dadd(s[k], dmul(tmin, d[k])), half));
+    int i = dir[k] > 0 ? i0 - 1 : i0 + 2;
+    i = i < 0 ? 0 : (i > n ? n : i);
+    idx[k] = i;
+    act[k] = true;
+    tn[k] = plane_param(i, half, s[k], d[k]);
+    for (int guard = 0; act[k] && tn[k] <= tmin && guard <= n + 2; ++guard) {
+      idx[k] += dir[k];
+      if (idx[k] < 0 || idx[k] > n)
+        act[k] = false;
+      else
+        tn[k] = plane_param(idx[k], half, s[k], d[k]);
+    }
+  }
+
+  int cnt = 0;
+  double cur = tmin;
+  for (int it = 0; it < 3 * n + 4; ++it) {
+    double nxt = tmax;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (act[k] && tn[k] < nxt) nxt = tn[k];
+    if (FILL) {
+      const double mid = dmul(dadd(cur, nxt), 0.5);
+      int v[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int iv = (int)floor(dadd(dadd(s[k], dmul(mid, d[k])), half));
+        v[k] = iv < 0 ? 0 : (iv > n - 1 ? n - 1 : iv);
+      }
+      cols[cnt] = (int32_t)(v[0] + n * (v[1] + n * v[2]));
+      vals[cnt] = (float)dmul(dsub(nxt, cur), dnorm);
+    }
+    ++cnt;
+    if (nxt >= tmax) break;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      for (int guard = 0; act[k] && tn[k] <= nxt && guard <= n + 2; ++guard) {
+        idx[k] += dir[k];
+        if (idx[k] < 0 || idx[k] > n)
+          act[k] = false;
+        else
+          tn[k] = plane_param(idx[k], half, s[k], d[k]);
+      }
+    }
+    cur = nxt;
+  }
+  return cnt;
+}
+
+__global__ void k_siddon_count(const ViewRec *__restrict__ views, int n, int Pu, int Pv, int kind,
+                               int64_t m, int64_t *__restrict__ counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t per = (int64_t)Pu * Pv;
+  const int v = (int)(i / per);
+  const int64_t rem = i - (int64_t)v * per;
+  const int q = (int)(rem / Pu);
+  const int p = (int)(rem - (int64_t)q * Pu);
+  double s[3], c[3];
+  endpoints(views[v].v, kind, Pu, Pv, p, q, s, c);
+  counts[i] = trace<false>(s, c, n, nullptr, nullptr);
+}
+
+__global__ void k_siddon_fill(const ViewRec *__restrict__ views, int n, int Pu, int Pv, int kind,
+                              int64_t m, const int64_t *__restrict__ row_ptr,
+                              int32_t *__restrict__ cols, float *__restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t per = (int64_t)Pu * Pv;
+  const int v = (int)(i / per);
+  const int64_t rem = i - (int64_t)v * per;
+  const int q = (int)(rem / Pu);
+  const int p = (int)(rem - (int64_t)q * Pu);
+  double s[3], c[3];
+  endpoints(views[v].v, kind, Pu, Pv, p, q, s, c);
+  const int64_t o = row_ptr[i];
+  trace<true>(s, c, n, cols + o, vals + o);
+}
+
+// ---- exclusive scan of int64 counts: out[0] = 0, out[i+1] = sum(in[0..i]) ----
+constexpr int kScanItems = 4;
+constexpr int kScanTile = TVR_BLOCK * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive(int64_t v, int64_t *total) {
+  __shared__ int64_t sh[TVR_BLOCK / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < TVR_BLOCK / 32 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < TVR_BLOCK / 32) sh[lane] = w;
+  }
+  __syncthreads();
+  const int64_t warp_off = warp > 0 ? sh[warp - 1] : 0;
+  *total = sh[TVR_BLOCK / 32 - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void k_scan_tiles(const int64_t *__restrict__ in, int64_t n, int64_t *__restrict__ out,
+                             int64_t *__restrict__ tile_sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems], local = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    local += v[k];
+  }
+  int64_t total;
+  int64_t run = block_exclusive(local, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the tile sums in place; writes the grand total.
+__global__ void k_scan_sums(int64_t *__restrict__ sums, int64_t tiles, int64_t *__restrict__ total_out) {
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < tiles; b0 += TVR_BLOCK) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < tiles ? sums[i] : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive(v, &tot);
+    if (i < tiles) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ sums) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += sums[i / kScanTile];
+}
+
+// ---- transpose ----
+__global__ void k_col_hist(const int32_t *__restrict__ col, int64_t nnz, int64_t *__restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    atomicAdd(reinterpret_cast<unsigned long long *>(cnt + col[e]), 1ull);
+}
+
+// One thread per CSR row scatters its entries; the slot within a column is
+// taken by an atomic counter, so the order is fixed afterwards by k_col_sort.
+__global__ void k_csc_scatter(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                              const float *__restrict__ val, int64_t m,
+                              const int64_t *__restrict__ col_ptr, int64_t *__restrict__ fill,
+                              int64_t *__restrict__ key, int32_t *__restrict__ row,
+                              float *__restrict__ cval) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    const int c = col[e];
+    const int64_t pos =
+        col_ptr[c] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(fill + c), 1ull);
+    key[pos] = e;
+    row[pos] = (int32_t)i;
+    cval[pos] = val[e];
+  }
+}
+
+// Sort each column by CSR position (= by row, then traversal order):
+// insertion sort, one thread per column.
+__global__ void k_col_sort(const int64_t *__restrict__ col_ptr, int64_t N, int64_t *__restrict__ key,
+                           int32_t *__restrict__ row, float *__restrict__ cval) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const int64_t lo = col_ptr[c], hi = col_ptr[c + 1];
+  for (int64_t a = lo + 1; a < hi; ++a) {
+    const int64_t k = key[a];
+    const int32_t r = row[a];
+    const float v = cval[a];
+    int64_t b = a - 1;
+    while (b >= lo && key[b] > k) {
+      key[b + 1] = key[b];
+      row[b + 1] = row[b];
+      cval[b + 1] = cval[b];
+      --b;
+    }
+    key[b + 1] = k;
+    row[b + 1] = r;
+    cval[b + 1] = v;
+  }
+}
+
+}  // namespace
+
+// Exclusive scan: out has n+1 entries; out[n] = total.  tmp: >= tiles + 1 int64.
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
+                               cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles > 0) {
+    k_scan_tiles<<<(unsigned)tiles, TVR_BLOCK, 0, s>>>(in, n, out, tmp);
+    k_scan_sums<<<1, TVR_BLOCK, 0, s>>>(tmp, tiles, out + n);
+    k_scan_add<<<(unsigned)((n + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(out, n, tmp);
+  } else {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  }
+  return cudaGetLastError();
+}
+
+int64_t scan_tmp_len(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t siddon_count(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                         int64_t *counts, cudaStream_t s) {
+  const unsigned grid = (unsigned)((m + 127) / 128);
+  k_siddon_count<<<grid, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv, kind,
+                                      m, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                        const int64_t *row_ptr, int32_t *cols, float *vals, cudaStream_t s) {
+  const unsigned grid = (unsigned)((m + 127) / 128);
+  k_siddon_fill<<<grid, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv, kind,
+                                     m, row_ptr, cols, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
+                       int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
+                       int64_t *cnt /*N*/, int64_t *key /*nnz*/, int64_t *tmp, cudaStream_t s) {
+  cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
+  if (nnz > 0) k_col_hist<<<1216, TVR_BLOCK, 0, s>>>(col, nnz, cnt);
+  cudaError_t e = scan_exclusive_i64(cnt, N, col_ptr, tmp, s);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
+  if (m > 0)
+    k_csc_scatter<<<(unsigned)((m + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(
+        row_ptr, col, val, m, col_ptr, cnt, key, row, cval);
+  if (N > 0)
+    k_col_sort<<<(unsigned)((N + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(col_ptr, N, key,
+                                                                                 row, cval);
+  return cudaGetLastError();
+}

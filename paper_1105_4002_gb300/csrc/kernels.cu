@@ -1,0 +1,470 @@
+// Hot-path kernels of the TV-CT gradient methods (sm_103a).
+//
+//   k_forward   r = A x - b (CSR, row-parallel), 1/2||r||^2; trial mode also A(x - p)
+//   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free) fused with
+//               the TV_tau stencil and its value; solver modes add the BB dots
+//               (GPBB) or the TV Bregman sum of the mu-estimate (UPN)
+//   k_step      xbar = P_Q(p - s g) with g^T d, ||d||^2, sum_j B_h (step + projection)
+//   k_yform     UPN extrapolation y = x+ + beta (x+ - x) and its residual A y - b
+//   k_tv_value  TV_tau(x) alone (phi without a gradient)
+//   k_project   P_Q in place; k_gmap gradient-map norm
+//
+// All reductions: double-single per thread / warp / block, deterministic
+// block-ordered finish in the last block (tvr_internal.cuh).
+#include "ctrl.cuh"
+#include "tvr_internal.cuh"
+
+#define FULL 0xffffffffu
+
+namespace {
+
+constexpr int kRowLanes = 8;  // lanes per CSR row
+constexpr int kColLanes = 8;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(FULL, v, o, G));
+  return v;
+}
+
+__device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
+
+enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3 };
+enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3 };
+
+// ---------------------------------------------------------------------------
+// Forward projection.  G lanes per row, rows of a warp are consecutive (rays
+// of neighbouring detector pixels, which share voxels: x gathers hit in L1).
+// ---------------------------------------------------------------------------
+template <int G, int MODE>
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
+              float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1) {
+  const float *x = xin;
+  const float *p = nullptr;
+  float *r = rout;
+  float *ad = nullptr;
+  if (MODE == FWD_INIT) {
+    const bool upn = st->solver == SOLVER_UPN;
+    b = st->b;
+    x = upn ? st->vN[RN_Y] : st->vN[RN_X];
+    r = upn ? st->vM[RM_RY] : st->vM[RM_R];
+  } else if (MODE == FWD_TRIAL) {
+    if (st->done) return;
+    if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->prof_flags[prof_slot] = 1;
+    const bool upn = st->solver == SOLVER_UPN;
+    b = st->b;
+    x = st->vN[RN_T];
+    p = upn ? st->vN[RN_Y] : st->vN[RN_X];
+    r = st->vM[RM_RT];
+    ad = upn ? st->vM[RM_AD] : nullptr;
+  }
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & (G - 1);
+  const int sub = (threadIdx.x & 31) / G;
+  const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
+  const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
+  FF a0 = ff_zero(), a1 = ff_zero();
+  for (int64_t base = warp * RPW; base < A.m; base += nwarp * RPW) {
+    const int64_t row = base + sub;
+    const bool valid = row < A.m;
+    int64_t beg = 0, end = 0;
+    if (valid) {
+      beg = __ldg(A.row_ptr + row);
+      end = __ldg(A.row_ptr + row + 1);
+    }
+    float sx = 0.f, sd = 0.f;
+    for (int64_t e = beg + lane; e < end; e += G) {
+      const int c = __ldg(A.col + e);
+      const float v = __ldg(A.val + e);
+      const float xv = __ldg(x + c);
+      sx = __fmaf_rn(v, xv, sx);
+      if (MODE == FWD_TRIAL) sd = __fmaf_rn(v, __fsub_rn(xv, __ldg(p + c)), sd);
+    }
+    sx = group_sum<G>(sx);
+    if (MODE == FWD_TRIAL) sd = group_sum<G>(sd);
+    if (valid && lane == 0) {
+      if (MODE == FWD_Y) {
+        r[row] = sx;
+      } else {
+        const float ri = __fsub_rn(sx, __ldg(b + row));
+        r[row] = ri;
+        ff_add_prod(a0, ri, ri);
+        if (MODE == FWD_TRIAL) {
+          if (ad) ad[row] = sd;
+          ff_add_prod(a1, sd, sd);
+        }
+      }
+    }
+  }
+  if (MODE == FWD_Y) return;
+  FF acc[2] = {a0, a1};
+  double tot[2];
+  if (grid_reduce<2>(acc, slot, tot) && threadIdx.x == 0) {
+    if (MODE == FWD_INIT) st->r_init[0] = tot[0];
+    if (MODE == FWD_TRIAL) {
+      st->r_fwd[0] = tot[0];
+      st->r_fwd[1] = tot[1];
+      ctrl_trial(st, tot);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Back projection fused with the TV_tau stencil.  G lanes per column (voxel);
+// lanes 0..3 of a group evaluate the Huber weights of voxels j, j-ex, j-ey,
+// j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
+// ---------------------------------------------------------------------------
+template <int G, int MODE>
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
+               float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
+               const double *__restrict__ data_in, double *phi_dev, DevState *st,
+               int prof_slot = -1) {
+  const float *r = rin;
+  const float *x = xin;
+  float *g = gout;
+  const float *q = nullptr;   // UPN: x^(k) for the Bregman sum at y^(k)
+  const float *xo = nullptr;  // GPBB: x^(k-1)
+  const float *go = nullptr;  // GPBB: g^(k-1)
+  int kind = SOLVER_NONE;
+  if (MODE == BWD_INIT || MODE == BWD_SOLVER) {
+    if (MODE == BWD_SOLVER && (st->done || !st->need_grad)) return;
+    if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
+      st->prof_flags[TVR_PROF_PAIRS + prof_slot] = 1;
+    kind = st->solver;
+    alpha = (float)st->alpha;
+    tau = (float)st->tau;
+    if (kind == SOLVER_UPN) {
+      x = st->vN[RN_Y];
+      r = st->vM[RM_RY];
+      g = st->vN[RN_G];
+      if (MODE == BWD_SOLVER) q = st->vN[RN_X];
+    } else {
+      x = st->vN[RN_X];
+      r = st->vM[RM_R];
+      g = st->vN[RN_G];
+      if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
+        g = st->vN[RN_GN];
+        xo = st->vN[RN_T];
+        go = st->vN[RN_G];
+      }
+    }
+  }
+  const int n = A.n;
+  const int64_t nn = (int64_t)n * n;
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & (G - 1);
+  const int sub = (threadIdx.x & 31) / G;
+  const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
+  const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
+  FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
+  for (int64_t base = warp * RPW; base < A.N; base += nwarp * RPW) {
+    const int64_t j = base + sub;
+    const bool valid = j < A.N;
+    int64_t beg = 0, end = 0;
+    if (valid) {
+      beg = __ldg(A.col_ptr + j);
+      end = __ldg(A.col_ptr + j + 1);
+    }
+    float s = 0.f;
+    for (int64_t e = beg + lane; e < end; e += G) {
+      const int i = __ldg(A.row + e);
+      s = __fmaf_rn(__ldg(A.cval + e), __ldg(r + i), s);
+    }
+    s = group_sum<G>(s);
+    if (MODE == BWD_ADJ) {
+      if (valid && lane == 0) g[j] = s;
+      continue;
+    }
+    const int iz = (int)(j / nn);
+    const int iy = (int)((j - (int64_t)iz * nn) / n);
+    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    Huber hw;
+    float c = 0.f;
+    if (valid && lane < 4) {
+      huber_at(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, hw);
+      c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2]) : hw.w[lane - 1];
+    }
+    c = __fadd_rn(c, __shfl_down_sync(FULL, c, 2, G));
+    c = __fadd_rn(c, __shfl_down_sync(FULL, c, 1, G));
+    if (valid && lane == 0) {
+      const float gj = __fmaf_rn(alpha, c, s);
+      g[j] = gj;
+      ff_add(a0, hw.h);
+      if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
+        const float sj = __fsub_rn(x[j], xo[j]);
+        ff_add_prod(a1, sj, __fsub_rn(gj, go[j]));
+        ff_add_prod(a2, sj, sj);
+      }
+      if (MODE == BWD_SOLVER && kind == SOLVER_UPN) {
+        float zb[3], dl[3];
+        diff3(q, ix, iy, iz, n, zb);
+        const float d0 = __fsub_rn(q[j], x[j]);
+        dl[0] = ix + 1 < n ? __fsub_rn(__fsub_rn(q[j + 1], x[j + 1]), d0) : 0.f;
+        dl[1] = iy + 1 < n ? __fsub_rn(__fsub_rn(q[j + n], x[j + n]), d0) : 0.f;
+        dl[2] = iz + 1 < n ? __fsub_rn(__fsub_rn(q[j + nn], x[j + nn]), d0) : 0.f;
+        ff_add(a1, huber_bregman(hw.z, hw.nrm, zb, dl, tau));
+      }
+    }
+  }
+  if (MODE == BWD_ADJ) return;
+  FF acc[3] = {a0, a1, a2};
+  double tot[3];
+  if (grid_reduce<3>(acc, slot, tot) && threadIdx.x == 0) {
+    if (MODE == BWD_GRAD) {
+      const double data = 0.5 * data_in[0];
+      if (phi_dev) {
+        phi_dev[0] = data + alpha_d * tot[0];
+        phi_dev[1] = data;
+        phi_dev[2] = tot[0];
+      }
+    } else if (MODE == BWD_INIT) {
+      ctrl_init(st, tot);
+    } else {
+      st->r_bwd[0] = tot[0];
+      st->r_bwd[1] = tot[1];
+      st->r_bwd[2] = tot[2];
+      ctrl_after_grad(st, tot);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projected step xbar = P_Q(p - s g) (eq. gradientmethod; Alg. 1, Alg. 2) with
+// the reductions of the acceptance tests.  xbar at the forward neighbours is
+// recomputed with the same expression, so the TV Bregman sum sees exactly the
+// stored values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TVR_BLOCK) k_step(MatDev A, RedSlot slot, DevState *st) {
+  if (st->done) return;
+  const bool upn = st->solver == SOLVER_UPN;
+  const float *__restrict__ p = upn ? st->vN[RN_Y] : st->vN[RN_X];
+  const float *__restrict__ g = st->vN[RN_G];
+  float *__restrict__ t = st->vN[RN_T];
+  const float s = (float)st->step;
+  const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
+  const float s2 = (float)st->step2;
+  const float tau = (float)st->tau;
+  const int n = A.n;
+  const int64_t nn = (int64_t)n * n;
+  FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero();
+  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+  for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < A.N; j += stride) {
+    const float pj = p[j], gj = g[j];
+    const float xb = proj(__fsub_rn(pj, __fmul_rn(s, gj)));
+    t[j] = xb;
+    const float d = __fsub_rn(xb, pj);
+    ff_add_prod(a0, gj, d);
+    ff_add_prod(a1, d, d);
+    if (want_g2) {
+      const float e = __fsub_rn(pj, proj(__fsub_rn(pj, __fmul_rn(s2, gj))));
+      ff_add_prod(a3, e, e);
+    }
+    const int iz = (int)(j / nn);
+    const int iy = (int)((j - (int64_t)iz * nn) / n);
+    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    float z[3], zb[3], dl[3];
+    const int64_t off[3] = {1, n, nn};
+    const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      if (in[e]) {
+        const float pk = p[j + off[e]], gk = g[j + off[e]];
+        const float xk = proj(__fsub_rn(pk, __fmul_rn(s, gk)));
+        z[e] = __fsub_rn(pk, pj);
+        zb[e] = __fsub_rn(xk, xb);
+        dl[e] = __fsub_rn(__fsub_rn(xk, pk), d);
+      } else {
+        z[e] = zb[e] = dl[e] = 0.f;
+      }
+    }
+    ff_add(a2, huber_bregman(z, norm3(z), zb, dl, tau));
+  }
+  FF acc[4] = {a0, a1, a2, a3};
+  double tot[4];
+  if (grid_reduce<4>(acc, slot, tot) && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st->r_step[k] = tot[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// UPN extrapolation (Alg. 3): y = x+ + beta (x+ - x) and, by linearity of A,
+//   u  = A(x+ - x) = A(x+ - y_prev) + beta_prev u_prev,
+//   A y - b = (A x+ - b) + beta u,
+// so the residual at y needs no projection.  Reductions: ||x+ - x||^2, ||u||^2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TVR_BLOCK) k_yform(MatDev A, RedSlot slot, DevState *st) {
+  if (st->done || !st->need_grad) return;
+  const float beta = (float)st->beta, bp = (float)st->beta_prev;
+  const float *__restrict__ X = st->vN[RN_X];
+  const float *__restrict__ T = st->vN[RN_T];
+  float *__restrict__ Y = st->vN[RN_Y];
+  const float *__restrict__ R = st->vM[RM_R];
+  const float *__restrict__ AD = st->vM[RM_AD];
+  float *__restrict__ U = st->vM[RM_U];
+  float *__restrict__ RY = st->vM[RM_RY];
+  FF a0 = ff_zero(), a1 = ff_zero();
+  const int64_t lim = A.N > A.m ? A.N : A.m;
+  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+  for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < lim; i += stride) {
+    if (i < A.N) {
+      const float xn = X[i];
+      const float dx = __fsub_rn(xn, T[i]);
+      Y[i] = __fmaf_rn(beta, dx, xn);
+      ff_add_prod(a0, dx, dx);
+    }
+    if (i < A.m) {
+      const float u = __fmaf_rn(bp, U[i], AD[i]);
+      U[i] = u;
+      RY[i] = __fmaf_rn(beta, u, R[i]);
+      ff_add_prod(a1, u, u);
+    }
+  }
+  FF acc[2] = {a0, a1};
+  double tot[2];
+  if (grid_reduce<2>(acc, slot, tot) && threadIdx.x == 0) {
+    st->r_yf[0] = tot[0];
+    st->r_yf[1] = tot[1];
+  }
+}
+
+// TV_tau(x) alone; finishes phi from the forward kernel's 1/2||r||^2.
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_tv_value(MatDev A, const float *__restrict__ x, float tau, double alpha_d, RedSlot slot,
+               const double *__restrict__ data_in, double *phi_dev) {
+  const int n = A.n;
+  const int64_t nn = (int64_t)n * n;
+  FF a0 = ff_zero();
+  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+  for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < A.N; j += stride) {
+    const int iz = (int)(j / nn);
+    const int iy = (int)((j - (int64_t)iz * nn) / n);
+    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    float z[3];
+    diff3(x, ix, iy, iz, n, z);
+    ff_add(a0, huber_h(norm3(z), tau));
+  }
+  FF acc[1] = {a0};
+  double tot[1];
+  if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0) {
+    const double data = 0.5 * data_in[0];
+    if (phi_dev) {
+      phi_dev[0] = data + alpha_d * tot[0];
+      phi_dev[1] = data;
+      phi_dev[2] = tot[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TVR_BLOCK) k_project(float *__restrict__ x, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+  for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < n; i += stride)
+    x[i] = proj(x[i]);
+}
+
+// ||G_nu(x)|| = nu ||x - P_Q(x - g / nu)||.
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_gmap(const float *__restrict__ x, const float *__restrict__ g, int64_t n, float inv_nu,
+           double nu, RedSlot slot) {
+  FF a0 = ff_zero();
+  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+  for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < n; i += stride) {
+    const float e = __fsub_rn(x[i], proj(__fsub_rn(x[i], __fmul_rn(g[i], inv_nu))));
+    ff_add_prod(a0, e, e);
+  }
+  FF acc[1] = {a0};
+  double tot[1];
+  if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0) slot.out[1] = nu * sqrt(tot[0]);
+}
+
+int elem_grid(int64_t n, int cap) {
+  int64_t b = (n + TVR_BLOCK - 1) / TVR_BLOCK;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+int occupancy_grid(const void *kernel, int block, int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0);
+  if (per < 1) per = 1;
+  int g = sms * per;
+  return g < TVR_MAX_GRID ? g : TVR_MAX_GRID;
+}
+
+void kernel_grids(Workspace &ws, int device) {
+  ws.grid_fwd = occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL>, TVR_BLOCK, device);
+  ws.grid_bwd = occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER>, TVR_BLOCK, device);
+  ws.grid_elem = occupancy_grid((const void *)k_step, TVR_BLOCK, device);
+}
+
+void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
+                    cudaStream_t s) {
+  k_forward<kRowLanes, FWD_RESID><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, b, r, ws.fwd, nullptr);
+}
+
+void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
+                          cudaStream_t s) {
+  k_forward<kRowLanes, FWD_Y><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, nullptr, y, ws.fwd, nullptr);
+}
+
+void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
+                     float *g, const Workspace &ws, double *phi_dev, cudaStream_t s) {
+  k_backward<kColLanes, BWD_GRAD><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, r, x, alpha, tau, (double)alpha, g, ws.bwd, ws.fwd.out, phi_dev, nullptr);
+}
+
+void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
+                          cudaStream_t s) {
+  k_backward<kColLanes, BWD_ADJ><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, r, nullptr, 0.f, 1.f, 0.0, z, ws.bwd, nullptr, nullptr, nullptr);
+}
+
+void launch_tv_value(const MatDev &A, const float *x, float alpha, float tau, const Workspace &ws,
+                     double *phi_dev, cudaStream_t s) {
+  k_tv_value<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, x, tau, (double)alpha, ws.tv,
+                                                                 ws.fwd.out, phi_dev);
+}
+
+void launch_project(float *x, int64_t n, cudaStream_t s) {
+  k_project<<<elem_grid(n, 4 * 152 * 8), TVR_BLOCK, 0, s>>>(x, n);
+}
+
+void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, const Workspace &ws,
+                      cudaStream_t s) {
+  k_gmap<<<elem_grid(n, ws.grid_elem), TVR_BLOCK, 0, s>>>(x, g, n, (float)(1.0 / nu), nu, ws.gmap);
+}
+
+void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
+  k_forward<kRowLanes, FWD_INIT><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr,
+                                                                   ws.fwd, st);
+  k_backward<kColLanes, BWD_INIT><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st);
+}
+
+// One pass: [UPN: extrapolation] -> gradient at the new point (skipped after a
+// rejected trial) -> projected trial step -> forward projection + test.
+void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
+                        cudaStream_t s, const PassTiming *tm) {
+  if (solver == SOLVER_UPN)
+    k_yform<<<elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.yf, st);
+  if (tm) cudaEventRecord(tm->ev[1][0], s);
+  k_backward<kColLanes, BWD_SOLVER><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st,
+      tm ? tm->slot[1] : -1);
+  if (tm) cudaEventRecord(tm->ev[1][1], s);
+  k_step<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.step, st);
+  if (tm) cudaEventRecord(tm->ev[0][0], s);
+  k_forward<kRowLanes, FWD_TRIAL><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr,
+                                                                    ws.fwd, st,
+                                                                    tm ? tm->slot[0] : -1);
+  if (tm) cudaEventRecord(tm->ev[0][1], s);
+}

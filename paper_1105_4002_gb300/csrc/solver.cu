@@ -1,0 +1,226 @@
+// GP / GPBB / UPN drivers.
+//
+// A solve is a sequence of identical "passes" (kernels.cu, launch_solver_pass):
+//   [UPN: y-extrapolation] -> gradient at the newly accepted point
+//   -> projected trial step -> forward projection + acceptance test.
+// Kernels whose work is not due (no new point yet, or the solve has stopped)
+// return at once after reading the device state, so the host never needs to
+// know the outcome of a line-search trial: it launches passes in batches --
+// replayed as one CUDA graph -- and reads a single "done" flag per batch.
+// Every data-dependent loop of the method is bounded on the device (k_max,
+// the trial caps), and the number of batches is bounded on the host.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "system.cuh"
+
+namespace {
+
+int ensure_solver(tvr_system *sys, int64_t hist_records) {
+  for (auto &p : sys->vN)
+    if (int rc = ensure_vec(&p, sys->N)) return rc;
+  for (auto &p : sys->vM)
+    if (int rc = ensure_vec(&p, sys->m)) return rc;
+  if (!sys->st) TVR_CUDA(cudaMalloc(&sys->st, sizeof(DevState)));
+  if (!sys->pinned_flag) TVR_CUDA(cudaMallocHost(&sys->pinned_flag, 64));
+  if (!sys->cap_stream) TVR_CUDA(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking));
+  if (hist_records > sys->hist_cap) {
+    if (sys->hist_dev) cudaFree(sys->hist_dev);
+    sys->hist_dev = nullptr;
+    sys->hist_cap = 0;
+    TVR_CUDA(cudaMalloc(&sys->hist_dev, sizeof(double) * TVR_HIST_FIELDS * hist_records));
+    sys->hist_cap = (int)hist_records;
+  }
+  return TVR_OK;
+}
+
+int pass_graph(tvr_system *sys, int solver, int batch, cudaGraphExec_t *out) {
+  if (sys->pass_graph[solver] && sys->pass_graph_batch[solver] == batch) {
+    *out = sys->pass_graph[solver];
+    return TVR_OK;
+  }
+  if (sys->pass_graph[solver]) {
+    cudaGraphExecDestroy(sys->pass_graph[solver]);
+    sys->pass_graph[solver] = nullptr;
+  }
+  const MatDev A = sys->mat();
+  TVR_CUDA(cudaStreamBeginCapture(sys->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < batch; ++i) launch_solver_pass(A, sys->st, solver, sys->ws, sys->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(sys->cap_stream, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(pass batch)");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(pass batch)");
+  sys->pass_graph[solver] = exec;
+  sys->pass_graph_batch[solver] = batch;
+  *out = exec;
+  return TVR_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int solve(const tvr_system *csys, int solver, const float *b, double alpha, double tau, double eps,
+          const tvr_solve_opts *uo, float *x, tvr_solve_info *info, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !b || !x) return fail(TVR_ERR_ARG, "tvr_solve: null argument");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha) || !finite_pos(tau) || !finite_pos(eps))
+    return fail(TVR_ERR_ARG, "tvr_solve: need alpha >= 0, tau > 0, eps > 0 (finite)");
+  tvr_solve_opts o;
+  tvr_solve_opts_default(&o);
+  if (uo) o = *uo;
+  if (o.k_max < 1 || o.gpbb_K < 0 || o.gpbb_K > 8 || o.gpbb_max_trials < 0 || o.bt_max < 0 ||
+      o.batch < 1 || o.batch > 1024 || !(o.rho_L > 1.0) || !std::isfinite(o.rho_L) ||
+      !finite_pos(o.L_bar) || !(o.mu_bar >= 0.0) || !std::isfinite(o.mu_bar) ||
+      !(o.gpbb_sigma > 0.0 && o.gpbb_sigma < 1.0) || !(o.gpbb_beta0 > 0.0 && o.gpbb_beta0 < 1.0) ||
+      (o.stop_mode != TVR_STOP_REL && o.stop_mode != TVR_STOP_PER_N) || o.history_len < 0 ||
+      (o.history_len > 0 && !o.history))
+    return fail(TVR_ERR_ARG, "tvr_solve: invalid options");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t hist_n = o.history ? (o.history_len < (1 << 30) ? o.history_len : (1 << 30)) : 0;
+  if (int rc = ensure_solver(sys, hist_n)) return rc;
+  const float *bd;
+  if (int rc = stage_in(b, sys->m, &sys->stage_bM, s, &bd)) return rc;
+  const bool xdev = is_device_ptr(x);
+  const cudaMemcpyKind kin = xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  TVR_CUDA(cudaMemcpyAsync(sys->vN[0], x, sizeof(float) * sys->N, kin, s));
+  if (solver == SOLVER_UPN) {
+    TVR_CUDA(cudaMemcpyAsync(sys->vN[2], sys->vN[0], sizeof(float) * sys->N,
+                             cudaMemcpyDeviceToDevice, s));
+    TVR_CUDA(cudaMemsetAsync(sys->vM[3], 0, sizeof(float) * sys->m, s));
+  }
+  DevState h;
+  std::memset(&h, 0, sizeof(h));
+  h.alpha = alpha;
+  h.tau = tau;
+  h.eps = eps;
+  h.rho = o.rho_L;
+  h.sigma = o.gpbb_sigma;
+  h.beta0 = o.gpbb_beta0;
+  h.Lbar = o.L_bar;
+  h.mubar = o.mu_bar;
+  h.kmax = o.k_max;
+  h.K = o.gpbb_K;
+  h.max_trials = o.gpbb_max_trials;
+  h.bt_max = o.bt_max;
+  h.stop_mode = o.stop_mode;
+  h.solver = solver;
+  h.N = sys->N;
+  h.b = bd;
+  for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
+  for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
+  h.hist = hist_n > 0 ? sys->hist_dev : nullptr;
+  h.prof_flags = sys->prof_flags_dev;
+  h.hist_cap = (int)hist_n;
+  TVR_CUDA(cudaMemcpyAsync(sys->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  const MatDev A = sys->mat();
+  launch_solver_init(A, sys->st, sys->ws, s);
+  TVR_CUDA(cudaGetLastError());
+
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graph && !sys->profile)
+    if (int rc = pass_graph(sys, solver, o.batch, &exec)) return rc;
+  const int64_t trials = (o.bt_max > o.gpbb_max_trials ? o.bt_max : o.gpbb_max_trials) + 2;
+  const int64_t max_passes = ((int64_t)o.k_max + 1) * trials + o.batch;
+  int64_t passes = 0;
+  bool done = false;
+  while (!done && passes < max_passes) {
+    if (exec) {
+      TVR_CUDA(cudaGraphLaunch(exec, s));
+    } else {
+      for (int i = 0; i < o.batch; ++i) {
+        PassTiming tm;
+        const PassTiming *tp = nullptr;
+        if (sys->profile) {
+          if (sys->prof_n[0] >= kProfPairs || sys->prof_n[1] >= kProfPairs)
+            if (int rc = prof_harvest(sys)) return rc;
+          const int a = prof_take(sys, 0, true), c = prof_take(sys, 1, true);
+          if (a >= 0 && c >= 0) {
+            for (int w = 0; w < 2; ++w) {
+              tm.ev[0][w] = sys->prof_ev[0][a][w];
+              tm.ev[1][w] = sys->prof_ev[1][c][w];
+            }
+            tm.slot[0] = a;
+            tm.slot[1] = c;
+            tp = &tm;
+          }
+        }
+        launch_solver_pass(A, sys->st, solver, sys->ws, s, tp);
+      }
+      TVR_CUDA(cudaGetLastError());
+    }
+    passes += o.batch;
+    TVR_CUDA(cudaMemcpyAsync(sys->pinned_flag, &sys->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TVR_CUDA(cudaStreamSynchronize(s));
+    done = *sys->pinned_flag != 0;
+  }
+  DevState f;
+  TVR_CUDA(cudaMemcpyAsync(&f, sys->st, sizeof(f), cudaMemcpyDeviceToHost, s));
+  TVR_CUDA(cudaStreamSynchronize(s));
+  const cudaMemcpyKind kout = xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  TVR_CUDA(cudaMemcpyAsync(x, f.vN[RN_X], sizeof(float) * sys->N, kout, s));
+  // phi at the returned point, evaluated afresh
+  launch_forward(A, f.vN[RN_X], bd, f.vM[RM_RT], sys->ws, s);
+  launch_tv_value(A, f.vN[RN_X], (float)alpha, (float)tau, sys->ws, sys->phi_ws, s);
+  TVR_CUDA(cudaGetLastError());
+  double phi[3] = {0, 0, 0};
+  TVR_CUDA(cudaMemcpyAsync(phi, sys->phi_ws, sizeof(phi), cudaMemcpyDeviceToHost, s));
+  int hist_used = 0;
+  if (hist_n > 0 && f.hist_used > 0) {
+    hist_used = f.hist_used;
+    TVR_CUDA(cudaMemcpyAsync(o.history, sys->hist_dev, sizeof(double) * TVR_HIST_FIELDS * hist_used,
+                             cudaMemcpyDeviceToHost, s));
+  }
+  TVR_CUDA(cudaStreamSynchronize(s));
+  const int status = f.done ? f.status : TVR_NOT_CONVERGED;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->iters = f.k;
+    info->f_evals = f.f_evals;
+    info->g_evals = f.g_evals;
+    info->trials = f.total_trials;
+    info->passes = (int32_t)passes;
+    info->history_used = hist_used;
+    info->phi = phi[0];
+    info->gnorm = f.gnorm;
+    info->gnorm0 = f.gnorm0;
+    info->stop_value = f.stopval;
+    info->L = solver == SOLVER_GPBB ? 1.0 / f.theta : f.L;
+    info->theta = f.theta;
+    info->mu = f.mu;
+  }
+  (void)t0;
+  if (status < 0) {
+    const char *what = status == TVR_ERR_LINESEARCH ? "line search hit its trial cap"
+                                                    : "non-finite control value";
+    fail(status, std::string("tvr_solve: ") + what);
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tvr_solve_gp(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                 const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream) {
+  return solve(sys, SOLVER_GP, b, alpha, tau, eps, opts, x, info, stream);
+}
+
+int tvr_solve_gpbb(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                   const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream) {
+  return solve(sys, SOLVER_GPBB, b, alpha, tau, eps, opts, x, info, stream);
+}
+
+int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
+                  const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream) {
+  return solve(sys, SOLVER_UPN, b, alpha, tau, eps, opts, x, info, stream);
+}
+
+}  // extern "C"

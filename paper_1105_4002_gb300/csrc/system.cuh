@@ -1,0 +1,147 @@
+// The opaque tvr_system and host helpers shared by api.cu and solver.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "tvr_internal.cuh"
+
+int tvr_fail(int status, const std::string &msg);
+int tvr_cuda_fail(cudaError_t e, const char *what);
+
+#define TVR_CUDA(call)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return tvr_cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kSlots = 6;
+constexpr int kProfPairs = TVR_PROF_PAIRS;
+
+struct tvr_system {
+  int device = 0;
+  int n = 0, V = 0, Pu = 0, Pv = 0, kind = 0;
+  int64_t m = 0, N = 0, nnz = 0;
+  int64_t *row_ptr = nullptr, *col_ptr = nullptr;
+  int32_t *col = nullptr, *row = nullptr;
+  float *val = nullptr, *cval = nullptr;
+  void *ws_mem = nullptr;
+  Workspace ws{};
+  // staging and scratch vectors (allocated on first use)
+  float *stage_xN = nullptr, *stage_gN = nullptr, *stage_bM = nullptr, *stage_rM = nullptr;
+  double *phi_ws = nullptr;  // 4 doubles
+  // solver workspace (allocated on first solve)
+  DevState *st = nullptr;
+  float *vN[RN_COUNT] = {};
+  float *vM[RM_COUNT] = {};
+  double *hist_dev = nullptr;
+  int hist_cap = 0;
+  int *pinned_flag = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pass_graph[4] = {};
+  int pass_graph_batch[4] = {};
+  // kernel timing: event pairs of launches not yet harvested; a pair counts
+  // if it was a plain launch or if its kernel set its device "did work" flag
+  int profile = 0;
+  cudaEvent_t prof_ev[2][kProfPairs][2] = {};
+  int prof_n[2] = {0, 0};
+  int prof_slot[2][kProfPairs] = {};   // -1: plain launch, else device flag slot
+  int *prof_flags_dev = nullptr;       // [2 * kProfPairs]
+  int *prof_flags_host = nullptr;      // pinned copy
+  double prof_ms[2] = {0.0, 0.0};
+  int64_t prof_cnt[2] = {0, 0};
+
+  MatDev mat() const {
+    MatDev A;
+    A.n = n;
+    A.m = m;
+    A.N = N;
+    A.nnz = nnz;
+    A.row_ptr = row_ptr;
+    A.col = col;
+    A.val = val;
+    A.col_ptr = col_ptr;
+    A.row = row;
+    A.cval = cval;
+    return A;
+  }
+};
+
+inline int fail(int status, const std::string &msg) { return tvr_fail(status, msg); }
+inline int cuda_fail(cudaError_t e, const char *what) { return tvr_cuda_fail(e, what); }
+
+inline bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int ensure_vec(float **p, int64_t len) {
+  if (*p) return TVR_OK;
+  TVR_CUDA(cudaMalloc(p, sizeof(float) * (len > 0 ? len : 1)));
+  return TVR_OK;
+}
+
+// Device pointer for an input vector: itself, or a staged copy of host data.
+inline int stage_in(const float *src, int64_t len, float **stage, cudaStream_t s, const float **out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return TVR_OK;
+  }
+  int rc = ensure_vec(stage, len);
+  if (rc) return rc;
+  TVR_CUDA(cudaMemcpyAsync(*stage, src, sizeof(float) * len, cudaMemcpyHostToDevice, s));
+  *out = *stage;
+  return TVR_OK;
+}
+
+// Add the durations of all recorded launches that did work; synchronises on
+// the recorded events.
+inline int prof_harvest(tvr_system *sys) {
+  bool dev = false;
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < sys->prof_n[k]; ++i) dev = dev || sys->prof_slot[k][i] >= 0;
+  for (int k = 0; k < 2; ++k)
+    if (sys->prof_n[k] > 0) TVR_CUDA(cudaEventSynchronize(sys->prof_ev[k][sys->prof_n[k] - 1][1]));
+  if (dev) {
+    TVR_CUDA(cudaMemcpy(sys->prof_flags_host, sys->prof_flags_dev, sizeof(int) * 2 * kProfPairs,
+                        cudaMemcpyDeviceToHost));
+    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * 2 * kProfPairs));
+  }
+  for (int k = 0; k < 2; ++k) {
+    for (int i = 0; i < sys->prof_n[k]; ++i) {
+      const int sl = sys->prof_slot[k][i];
+      if (sl >= 0 && !sys->prof_flags_host[k * kProfPairs + sl]) continue;
+      float ms = 0.f;
+      TVR_CUDA(cudaEventElapsedTime(&ms, sys->prof_ev[k][i][0], sys->prof_ev[k][i][1]));
+      sys->prof_ms[k] += ms;
+      sys->prof_cnt[k] += 1;
+    }
+    sys->prof_n[k] = 0;
+  }
+  return TVR_OK;
+}
+
+// Next event pair of kind k (-1 when profiling is off or the pool is full;
+// callers harvest at points where no taken pair is still unrecorded).
+inline int prof_take(tvr_system *sys, int k, bool device_flag) {
+  if (!sys->profile || sys->prof_n[k] >= kProfPairs) return -1;
+  const int i = sys->prof_n[k]++;
+  sys->prof_slot[k][i] = device_flag ? i : -1;
+  return i;
+}
+
+inline void prof_mark(tvr_system *sys, int kind, int which, cudaStream_t s) {
+  if (!sys->profile) return;
+  if (which == 0) {
+    if (sys->prof_n[kind] >= kProfPairs) prof_harvest(sys);
+    const int i = prof_take(sys, kind, false);
+    if (i >= 0) cudaEventRecord(sys->prof_ev[kind][i][0], s);
+  } else if (sys->prof_n[kind] > 0) {
+    cudaEventRecord(sys->prof_ev[kind][sys->prof_n[kind] - 1][1], s);
+  }
+}

@@ -1,0 +1,319 @@
+// Internal declarations of libtvr: device helpers, solver state, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tvr.h"
+
+#define TVR_BLOCK 256          // threads per block of every streaming kernel
+#define TVR_RMAX 4             // reductions carried by one kernel
+#define TVR_MAX_GRID 4096      // upper bound on blocks of a reducing kernel
+#define TVR_PROF_PAIRS 4096    // timed launches held per kernel kind between harvests
+
+// ---------------------------------------------------------------------------
+// Double-single ("float-float") accumulation.
+//
+// GB300 executes FP64 at about 1/64 of the FP32 rate, so per-element FP64
+// arithmetic would cost more than the HBM traffic of the streaming kernels.
+// Sums are therefore carried as an unevaluated pair hi + lo of floats:
+// TwoSum (Knuth) gives the exact rounding error of each addition and TwoProd
+// (via fmaf) the exact error of each product, so a product of two floats is
+// accumulated without loss and the pair keeps about 48 significant bits.  The
+// pair is turned into a double once per reduction.  Every combination order
+// is fixed, so the results are deterministic.
+// ---------------------------------------------------------------------------
+struct __align__(8) FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_zero() { return FF{0.f, 0.f}; }
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void ff_add(FF &a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+// a += x * y with the product's rounding error kept.
+__device__ __forceinline__ void ff_add_prod(FF &a, float x, float y) {
+  float p = __fmul_rn(x, y);
+  float pe = __fmaf_rn(x, y, -p);
+  ff_add(a, p);
+  a.lo = __fadd_rn(a.lo, pe);
+}
+
+__device__ __forceinline__ FF ff_merge(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float hi = __fadd_rn(s, e);
+  float lo = __fsub_rn(e, __fsub_rn(hi, s));
+  return FF{hi, lo};
+}
+
+__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
+  FF b;
+  b.hi = __shfl_down_sync(0xffffffffu, a.hi, off);
+  b.lo = __shfl_down_sync(0xffffffffu, a.lo, off);
+  return b;
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Reduction workspace of one kernel: per-block partials and an arrival counter.
+struct RedSlot {
+  FF *partials;        // [TVR_MAX_GRID * TVR_RMAX]
+  unsigned *counter;   // reset to 0 by the finishing block
+  double *out;         // [TVR_RMAX] final sums (FP64)
+};
+
+// Block-wide reduction of R pairs; the result is valid in thread 0.
+template <int R>
+__device__ __forceinline__ void block_reduce(FF (&a)[R]) {
+  __shared__ FF sh[TVR_BLOCK / 32][R];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] = ff_merge(a[k], ff_shfl_down(a[k], o));
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < R; ++k) sh[warp][k] = a[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      a[k] = lane < TVR_BLOCK / 32 ? sh[lane][k] : ff_zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a[k] = ff_merge(a[k], ff_shfl_down(a[k], o));
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide deterministic reduction.  Every block stores its partial; the last
+// block to arrive sums all partials in block order and returns true in all of
+// its threads, with the FP64 totals in `tot` (valid in thread 0) and in
+// slot.out.  No thread ever waits on another block.
+template <int R>
+__device__ __forceinline__ bool grid_reduce(FF (&a)[R], const RedSlot &slot, double (&tot)[R]) {
+  __shared__ bool am_last;
+  block_reduce<R>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) slot.partials[blockIdx.x * R + k] = a[k];
+    __threadfence();
+    unsigned t = atomicAdd(slot.counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  FF s[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) s[k] = ff_zero();
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += TVR_BLOCK) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const float2 v = __ldcg(reinterpret_cast<const float2 *>(slot.partials + i * R + k));
+      s[k] = ff_merge(s[k], FF{v.x, v.y});
+    }
+  }
+  block_reduce<R>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      tot[k] = ff_to_double(s[k]);
+      slot.out[k] = tot[k];
+    }
+    *slot.counter = 0u;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Huber weight of one voxel: z = D_k x (forward differences, 0 across the
+// border), returns w = z / max(tau, |z|), |z| and h_tau(z).  A voxel outside
+// the grid yields w = 0.
+// ---------------------------------------------------------------------------
+struct Huber {
+  float z[3];
+  float w[3];
+  float nrm;
+  float h;
+};
+
+__device__ __forceinline__ float huber_h(float nrm, float tau) {
+  return nrm >= tau ? __fsub_rn(nrm, 0.5f * tau) : __fdiv_rn(__fmul_rn(nrm, nrm), 2.f * tau);
+}
+
+__device__ __forceinline__ void diff3(const float *__restrict__ x, int ix, int iy, int iz, int n,
+                                      float z[3]) {
+  const int64_t j = (int64_t)ix + (int64_t)n * (iy + (int64_t)n * iz);
+  const float c = __ldg(x + j);
+  z[0] = ix + 1 < n ? __fsub_rn(__ldg(x + j + 1), c) : 0.f;
+  z[1] = iy + 1 < n ? __fsub_rn(__ldg(x + j + n), c) : 0.f;
+  z[2] = iz + 1 < n ? __fsub_rn(__ldg(x + j + (int64_t)n * n), c) : 0.f;
+}
+
+__device__ __forceinline__ float norm3(const float z[3]) {
+  return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(z[0], z[0]), __fmul_rn(z[1], z[1])),
+                              __fmul_rn(z[2], z[2])));
+}
+
+__device__ __forceinline__ void huber_at(const float *__restrict__ x, int ix, int iy, int iz,
+                                         int n, float tau, Huber &o) {
+  if (ix < 0 || iy < 0 || iz < 0) {
+    o.z[0] = o.z[1] = o.z[2] = 0.f;
+    o.w[0] = o.w[1] = o.w[2] = 0.f;
+    o.nrm = 0.f;
+    o.h = 0.f;
+    return;
+  }
+  diff3(x, ix, iy, iz, n, o.z);
+  o.nrm = norm3(o.z);
+  const float den = fmaxf(tau, o.nrm);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) o.w[e] = __fdiv_rn(o.z[e], den);
+  o.h = huber_h(o.nrm, tau);
+}
+
+// Bregman divergence of h_tau at base z evaluated at zb = z + dlt:
+//   h(zb) - h(z) - w(z) . dlt  (>= 0),
+// in a form without cancellation when both points lie in the same zone:
+//   quadratic zone: |dlt|^2 / (2 tau);
+//   linear zone:    |z x dlt|^2 / (|z| (|zb||z| + z.zb))  when z.zb > 0.
+__device__ __forceinline__ float huber_bregman(const float z[3], float nz, const float zb[3],
+                                               const float dlt[3], float tau) {
+  const float nb = norm3(zb);
+  if (nz < tau && nb < tau) {
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dlt[0], dlt[0]), __fmul_rn(dlt[1], dlt[1])),
+                               __fmul_rn(dlt[2], dlt[2]));
+    return __fdiv_rn(d2, 2.f * tau);
+  }
+  const float dot = __fadd_rn(__fadd_rn(__fmul_rn(z[0], zb[0]), __fmul_rn(z[1], zb[1])),
+                              __fmul_rn(z[2], zb[2]));
+  if (nz >= tau && nb >= tau && dot > 0.f) {
+    const float c0 = __fsub_rn(__fmul_rn(z[1], dlt[2]), __fmul_rn(z[2], dlt[1]));
+    const float c1 = __fsub_rn(__fmul_rn(z[2], dlt[0]), __fmul_rn(z[0], dlt[2]));
+    const float c2 = __fsub_rn(__fmul_rn(z[0], dlt[1]), __fmul_rn(z[1], dlt[0]));
+    const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+    return __fdiv_rn(cc, __fmul_rn(nz, __fadd_rn(__fmul_rn(nb, nz), dot)));
+  }
+  const float den = fmaxf(tau, nz);
+  const float wd = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(z[0], dlt[0]), __fmul_rn(z[1], dlt[1])),
+                                       __fmul_rn(z[2], dlt[2])),
+                             den);
+  const float b = __fsub_rn(__fsub_rn(huber_h(nb, tau), huber_h(nz, tau)), wd);
+  return fmaxf(b, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Solver state, resident in device memory.  Control scalars are FP64 and are
+// only touched by one thread (the finishing block of a reducing kernel).
+// Vector roles are pointers that the control logic swaps on acceptance.
+// ---------------------------------------------------------------------------
+enum SolverKind { SOLVER_NONE = 0, SOLVER_GP = 1, SOLVER_GPBB = 2, SOLVER_UPN = 3 };
+
+enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_COUNT };
+enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_COUNT };
+
+#define TVR_FHIST 16
+
+struct DevState {
+  // configuration
+  double alpha, tau, eps, rho, sigma, beta0, Lbar, mubar;
+  int kmax, K, max_trials, bt_max, stop_mode, solver;
+  int64_t N;
+  const float *b;  // data vector (device)
+  // control scalars
+  double L, Lt, theta, beta, beta_prev, mu, M;
+  int M_valid;
+  double step, step2;           // step size of the step kernel; GPBB: theta for G
+  double f_cur, fhist[TVR_FHIST];
+  int nhist;
+  double gnorm, gnorm0, stopval, gnorm_trial;
+  int k, trial, need_grad, done, status;
+  int total_trials, f_evals, g_evals;
+  // reduction results
+  double r_init[TVR_RMAX], r_fwd[TVR_RMAX], r_bwd[TVR_RMAX], r_step[TVR_RMAX], r_yf[TVR_RMAX];
+  // vector roles
+  float *vN[RN_COUNT];
+  float *vM[RM_COUNT];
+  // history (device buffer of hist_cap records)
+  double *hist;
+  int hist_cap, hist_used;
+  // kernel-timing flags: prof_flags[kind * TVR_PROF_PAIRS + slot] = 1 when a
+  // timed launch did work (kind 0 forward, 1 back projection)
+  int *prof_flags;
+};
+
+// ---------------------------------------------------------------------------
+// Device views of A and launch shapes.
+// ---------------------------------------------------------------------------
+struct MatDev {
+  int n;
+  int64_t m, N, nnz;
+  const int64_t *row_ptr;  // CSR [m+1]
+  const int32_t *col;      // [nnz]
+  const float *val;        // [nnz]
+  const int64_t *col_ptr;  // CSC [N+1]
+  const int32_t *row;      // [nnz]
+  const float *cval;       // [nnz]
+};
+
+struct Workspace {
+  RedSlot fwd, bwd, step, yf, tv, gmap;
+  int grid_fwd, grid_bwd, grid_elem;
+};
+
+// Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from
+// the device state); st == nullptr is the plain mode with explicit pointers.
+void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
+                    cudaStream_t s);
+void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
+                          cudaStream_t s);
+void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
+                     float *g, const Workspace &ws, double *phi_dev, cudaStream_t s);
+void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
+                          cudaStream_t s);
+void launch_tv_value(const MatDev &A, const float *x, float alpha, float tau, const Workspace &ws,
+                     double *phi_dev, cudaStream_t s);
+void launch_project(float *x, int64_t n, cudaStream_t s);
+void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, const Workspace &ws,
+                      cudaStream_t s);
+
+// Solver-mode launchers (pointers and scalars come from the device state).
+void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s);
+// Optional CUDA-event timing of the forward (kind 0) and back projection
+// (kind 1) launches of one pass: events recorded around each launch, and the
+// launch's slot for its "did work" flag.
+struct PassTiming {
+  cudaEvent_t ev[2][2];
+  int slot[2];
+};
+void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
+                        cudaStream_t s, const PassTiming *timing = nullptr);
+
+// Construction of A (build_system.cu).
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
+                               cudaStream_t s);
+int64_t scan_tmp_len(int64_t n);
+cudaError_t siddon_count(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                         int64_t *counts, cudaStream_t s);
+cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                        const int64_t *row_ptr, int32_t *cols, float *vals, cudaStream_t s);
+cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
+                       int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
+                       int64_t *cnt, int64_t *key, int64_t *tmp, cudaStream_t s);
+
+int occupancy_grid(const void *kernel, int block, int device);
+void kernel_grids(Workspace &ws, int device);

@@ -1,0 +1,169 @@
+"""GP / GPBB / UPN on the GPU vs the FP64 oracle (Alg. 1-3, Sec. III-D).
+
+x* parity target: 1e-4 relative L2 at equal eps.  The first iterations are
+also compared step by step (same accepted trials, gradient-map norms within
+float32 tolerance), before the FP32 and FP64 trajectories may part at a
+line-search decision that lies within rounding of its threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import cuda, dev_f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["gp", "gpbb", "upn"]
+ORACLE = {"gp": oracle.solve_gp, "gpbb": oracle.solve_gpbb, "upn": oracle.solve_upn}
+XSTAR_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def c32():
+    torch = cuda()
+    from paper_1105_4002_gb300 import System
+    cfg = synth.get_config("c32")
+    prob, geom, x_true = oracle.problem_from_config(cfg)
+    return torch, System(geom), prob, cfg
+
+
+@pytest.fixture(scope="module")
+def oracle_solutions(c32):
+    _, _, prob, cfg = c32
+    x0 = np.zeros(prob.N)
+    return {m: ORACLE[m](prob, x0, cfg.eps, oracle.Options(record=True)) for m in METHODS}
+
+
+def gpu_solve(c32, method, eps=None, **kw):
+    torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions
+    x = torch.zeros(prob.N, device="cuda")
+    o = SolveOptions(history=20000, **kw)
+    res = s.solve(method, dev_f32(torch, prob.b), prob.alpha, prob.tau, eps or cfg.eps, x, o)
+    return res, x.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_first_iterations_follow_the_oracle(c32, oracle_solutions, method):
+    res, _ = gpu_solve(c32, method)
+    ref = oracle_solutions[method]
+    h = res.history
+    k = min(8, len(ref.history), len(h))
+    for i in range(k):
+        r = ref.history[i]
+        assert int(h[i, 5]) == r["trials"], (i, h[i], r)
+        assert abs(h[i, 1] - r["gnorm"]) <= 1e-4 * r["gnorm"], (i, h[i, 1], r["gnorm"])
+
+
+@pytest.mark.parametrize("method", ["gp", "upn"])
+def test_xstar_matches_oracle_at_equal_eps(c32, oracle_solutions, method):
+    res, x = gpu_solve(c32, method)
+    ref = oracle_solutions[method]
+    assert res.status == 0 and ref.status == 0
+    _, _, prob, _ = c32
+    assert abs(res.phi - prob.f(ref.x)) <= 1e-5 * abs(prob.f(ref.x))
+    assert rel_l2(x, ref.x) <= XSTAR_TOL, (method, rel_l2(x, ref.x), res.iters, ref.iters)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5])
+def test_gpbb_xstar_within_the_oracles_own_sensitivity(c32, eps):
+    """GPBB stops on ||G_{1/theta_k}||, and theta_k (the BB step) reacts to
+    rounding-size changes of the data, so its stopping point at a loose eps is
+    not a continuous function of the inputs: the FP64 oracle itself, given b
+    perturbed at the relative size of float32 gradient error (1e-6, seeded),
+    returns x* up to ~1e-2 (eps = 1e-4) or ~3e-4 (eps = 1e-5) apart.  The GPU
+    result must lie within twice that spread of the oracle's (or within the
+    1e-4 target)."""
+    _, _, prob, _ = c32
+    x0 = np.zeros(prob.N)
+    a = oracle.solve_gpbb(prob, x0, eps)
+    rng = np.random.default_rng(0)
+    spread, fspread = 0.0, 0.0
+    for _ in range(4):
+        pb = prob.b * (1 + 1e-6 * rng.standard_normal(prob.b.size))
+        pert = oracle.Problem(A=prob.A, b=pb, n=prob.n, alpha=prob.alpha, tau=prob.tau)
+        r = oracle.solve_gpbb(pert, x0, eps)
+        spread = max(spread, rel_l2(r.x, a.x))
+        fspread = max(fspread, abs(prob.f(r.x) - prob.f(a.x)))
+    res, x = gpu_solve(c32, "gpbb", eps=eps)
+    assert res.status == 0 and a.status == 0
+    assert rel_l2(x, a.x) <= max(XSTAR_TOL, 2 * spread), (rel_l2(x, a.x), spread)
+    assert abs(res.phi - prob.f(a.x)) <= max(1e-5 * prob.f(a.x), 2 * fspread)
+
+
+def test_graph_and_direct_launches_agree_bitwise(c32):
+    r1, x1 = gpu_solve(c32, "upn", use_graph=True)
+    r2, x2 = gpu_solve(c32, "upn", use_graph=False, batch=7)
+    assert np.array_equal(x1, x2) and r1.iters == r2.iters and r1.gnorm == r2.gnorm
+
+
+def test_solves_are_deterministic(c32):
+    r1, x1 = gpu_solve(c32, "gpbb")
+    r2, x2 = gpu_solve(c32, "gpbb")
+    assert np.array_equal(x1, x2) and r1.iters == r2.iters
+
+
+def test_host_buffers(c32):
+    torch, s, prob, cfg = c32
+    x = np.zeros(prob.N, np.float32)
+    res = s.solve("upn", prob.b.astype(np.float32), prob.alpha, prob.tau, cfg.eps, x)
+    _, xd = gpu_solve(c32, "upn")
+    assert res.ok and np.array_equal(x.astype(np.float64), xd)
+
+
+def test_status_paths(c32):
+    torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions, TVRError
+    b = dev_f32(torch, prob.b)
+    x = torch.zeros(prob.N, device="cuda")
+    r = s.solve("upn", b, prob.alpha, prob.tau, 1e-12, x, SolveOptions(k_max=5))
+    assert r.status == 1 and r.iters == 5                 # TVR_NOT_CONVERGED
+    with pytest.raises(TVRError) as e:                     # BT may not raise L at all
+        s.solve("gp", b, prob.alpha, prob.tau, 1e-4, torch.zeros_like(x), SolveOptions(bt_max=0))
+    assert e.value.status == -4
+    with pytest.raises(TVRError) as e:                     # theta_0 = 1 is far too long a step
+        s.solve("gpbb", b, prob.alpha, prob.tau, 1e-4, torch.zeros_like(x),
+                SolveOptions(gpbb_max_trials=0))
+    assert e.value.status == -4
+    bad = prob.b.copy()
+    bad[5] = np.nan
+    with pytest.raises(TVRError) as e:
+        s.solve("gpbb", dev_f32(torch, bad), prob.alpha, prob.tau, 1e-4, torch.zeros_like(x))
+    assert e.value.status == -5
+    with pytest.raises(TVRError) as e:
+        s.solve("upn", b, prob.alpha, prob.tau, -1.0, x)
+    assert e.value.status == -1
+
+
+def test_upn_mu_nonincreasing_and_bt_inequality(c32):
+    res, _ = gpu_solve(c32, "upn")
+    h = res.history
+    mus = h[1:, 3]
+    assert np.all(np.diff(mus) <= 0)
+    Ls = h[:, 2]
+    assert np.all(np.diff(Ls) >= 0)
+
+
+def test_4cubed_brute_force():
+    """Tiny few-view TV problem: every GPU method reaches the L-BFGS-B minimiser."""
+    torch = cuda()
+    import scipy.optimize as so
+    from conftest import small_geometry
+    from paper_1105_4002_gb300 import SolveOptions, System
+    g = small_geometry(n=4, views=3, det=5)
+    A = oracle.system_matrix(g)
+    rng = np.random.default_rng(12)
+    x_true = np.zeros(64)
+    x_true[rng.choice(64, 20, replace=False)] = rng.uniform(0.3, 1.0, 20)
+    b = (A @ x_true + 0.01 * rng.normal(size=g.m)).astype(np.float32).astype(np.float64)
+    prob = oracle.Problem(A=A, b=b, n=4, alpha=0.05, tau=1e-2)
+    ref = so.minimize(lambda x: prob.f_and_grad(x), np.zeros(64), jac=True, method="L-BFGS-B",
+                      bounds=[(0, None)] * 64,
+                      options=dict(maxiter=100000, ftol=1e-16, gtol=1e-13, maxcor=50)).x
+    s = System(g)
+    for method in METHODS:
+        x = torch.zeros(64, device="cuda")
+        res = s.solve(method, dev_f32(torch, b), 0.05, 1e-2, 1e-5, x, SolveOptions(k_max=200000))
+        assert res.ok, (method, res)
+        assert rel_l2(x.cpu().numpy(), ref) <= 1e-3, method
