@@ -84,7 +84,8 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   tvr_system *sys = new tvr_system();
   int rc = TVR_OK;
   double *views_dev = nullptr;
-  int64_t *counts = nullptr, *tmp = nullptr, *key = nullptr, *ccnt = nullptr;
+  int64_t *counts = nullptr, *tmp = nullptr, *ccnt = nullptr;
+  char *key = nullptr;
   auto cleanup = [&]() {
     if (views_dev) cudaFree(views_dev);
     if (counts) cudaFree(counts);
@@ -132,7 +133,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   BUILD_CUDA(cudaMalloc(&sys->col_ptr, sizeof(int64_t) * (N + 1)));
   BUILD_CUDA(cudaMalloc(&sys->row, sizeof(int32_t) * nz1));
   BUILD_CUDA(cudaMalloc(&sys->cval, sizeof(float) * nz1));
-  BUILD_CUDA(cudaMalloc(&key, sizeof(int64_t) * nz1));
+  BUILD_CUDA(cudaMalloc(&key, csc_tmp_bytes(nnz, N)));
   BUILD_CUDA(cudaMalloc(&ccnt, sizeof(int64_t) * N));
   BUILD_CUDA(csr_to_csc(sys->row_ptr, sys->col, sys->val, m, N, nnz, sys->col_ptr, sys->row,
                         sys->cval, ccnt, key, tmp, s));

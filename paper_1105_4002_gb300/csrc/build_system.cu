@@ -231,53 +231,97 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
   if (i < n) out[i] += sums[i / kScanTile];
 }
 
-// ---- transpose ----
+// ---- transpose: stable LSD radix sort of the CSR entries by column ----
+//
+// The CSR entries are already in row order, so a stable sort by column gives
+// the CSC order (rows ascending within a column) without any per-column sort.
+// Each pass sorts by one 8-bit digit of the column.  Work unit: one warp walks
+// kSubItems consecutive entries in chunks of 32; within a chunk,
+// __match_any_sync groups lanes with equal digits and the rank of a lane is
+// the number of lower lanes in its group, so the order inside a chunk, a
+// warp's range and the whole array is kept.  Offsets come from an exclusive
+// scan of the per-(digit, warp-range) counts in digit-major order.
+constexpr int kSubItems = 8192;                 // entries per warp range
+constexpr int kWarpsPerBlock = TVR_BLOCK / 32;  // 8
+
 __global__ void k_col_hist(const int32_t *__restrict__ col, int64_t nnz, int64_t *__restrict__ cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
     atomicAdd(reinterpret_cast<unsigned long long *>(cnt + col[e]), 1ull);
 }
 
-// One thread per CSR row scatters its entries; the slot within a column is
-// taken by an atomic counter, so the order is fixed afterwards by k_col_sort.
-__global__ void k_csc_scatter(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                              const float *__restrict__ val, int64_t m,
-                              const int64_t *__restrict__ col_ptr, int64_t *__restrict__ fill,
-                              int64_t *__restrict__ key, int32_t *__restrict__ row,
-                              float *__restrict__ cval) {
+__global__ void k_row_of(const int64_t *__restrict__ row_ptr, int64_t m, int32_t *__restrict__ row_of) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-    const int c = col[e];
-    const int64_t pos =
-        col_ptr[c] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(fill + c), 1ull);
-    key[pos] = e;
-    row[pos] = (int32_t)i;
-    cval[pos] = val[e];
+  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) row_of[e] = (int32_t)i;
+}
+
+template <typename P>
+__global__ void k_iota(P *__restrict__ out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (P)i;
+}
+
+// hist[d * nsub + sub] = entries of warp range `sub` whose digit is d.
+__global__ void k_radix_hist(const int32_t *__restrict__ key, int64_t n, int shift, int64_t nsub,
+                             int64_t *__restrict__ hist) {
+  __shared__ unsigned cnt[kWarpsPerBlock][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = lane; d < 256; d += 32) cnt[w][d] = 0u;
+  __syncwarp();
+  const int64_t sub = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (sub < nsub) {
+    const int64_t base = sub * kSubItems;
+    for (int c = 0; c < kSubItems; c += 32) {
+      const int64_t i = base + c + lane;
+      if (i < n) atomicAdd(&cnt[w][(key[i] >> shift) & 255], 1u);
+    }
+  }
+  __syncwarp();
+  if (sub < nsub)
+    for (int d = lane; d < 256; d += 32) hist[(int64_t)d * nsub + sub] = cnt[w][d];
+}
+
+template <typename P>
+__global__ void k_radix_scatter(const int32_t *__restrict__ key_in, const P *__restrict__ pay_in,
+                                int64_t n, int shift, int64_t nsub,
+                                const int64_t *__restrict__ offs, int32_t *__restrict__ key_out,
+                                P *__restrict__ pay_out) {
+  __shared__ int64_t run[kWarpsPerBlock][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t sub = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  for (int d = lane; d < 256; d += 32) run[w][d] = sub < nsub ? offs[(int64_t)d * nsub + sub] : 0;
+  __syncwarp();
+  if (sub >= nsub) return;  // whole warp leaves together
+  const unsigned lower = (1u << lane) - 1u;
+  const int64_t base = sub * kSubItems;
+  for (int c = 0; c < kSubItems; c += 32) {
+    const int64_t i = base + c + lane;
+    const bool ok = i < n;
+    const int32_t k = ok ? key_in[i] : 0;
+    const int d = ok ? (k >> shift) & 255 : 256;  // 256: lanes past the end form their own group
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lower);
+    if (ok) {
+      const int64_t pos = run[w][d] + rank;
+      key_out[pos] = k;
+      pay_out[pos] = pay_in[i];
+    }
+    __syncwarp();
+    if (ok && rank == 0) run[w][d] += __popc(peers);
+    __syncwarp();
   }
 }
 
-// Sort each column by CSR position (= by row, then traversal order):
-// insertion sort, one thread per column.
-__global__ void k_col_sort(const int64_t *__restrict__ col_ptr, int64_t N, int64_t *__restrict__ key,
-                           int32_t *__restrict__ row, float *__restrict__ cval) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= N) return;
-  const int64_t lo = col_ptr[c], hi = col_ptr[c + 1];
-  for (int64_t a = lo + 1; a < hi; ++a) {
-    const int64_t k = key[a];
-    const int32_t r = row[a];
-    const float v = cval[a];
-    int64_t b = a - 1;
-    while (b >= lo && key[b] > k) {
-      key[b + 1] = key[b];
-      row[b + 1] = row[b];
-      cval[b + 1] = cval[b];
-      --b;
-    }
-    key[b + 1] = k;
-    row[b + 1] = r;
-    cval[b + 1] = v;
+template <typename P>
+__global__ void k_csc_gather(const P *__restrict__ perm, int64_t nnz, const int32_t *__restrict__ row_of,
+                             const float *__restrict__ val, int32_t *__restrict__ row,
+                             float *__restrict__ cval) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+    const int64_t e = (int64_t)perm[k];
+    row[k] = row_of[e];
+    cval[k] = val[e];
   }
 }
 
@@ -315,19 +359,66 @@ cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind
   return cudaGetLastError();
 }
 
+// Bytes of temporary device memory csr_to_csc needs.
+size_t csc_tmp_bytes(int64_t nnz, int64_t N) {
+  const size_t pay = nnz >= ((int64_t)1 << 31) ? 8 : 4;
+  const int64_t nsub = (nnz + kSubItems - 1) / kSubItems;
+  const int64_t nh = 256 * (nsub > 0 ? nsub : 1);
+  return (size_t)nnz * (4 + 4 + 4 + 2 * pay) + sizeof(int64_t) * (2 * nh + scan_tmp_len(nh) + N) + 4096;
+}
+
+namespace {
+
+template <typename P>
+cudaError_t radix_transpose(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
+                            int64_t N, int64_t nnz, int32_t *row, float *cval, char *tmp,
+                            cudaStream_t s) {
+  const int64_t nsub = (nnz + kSubItems - 1) / kSubItems;
+  const int64_t nh = 256 * nsub;
+  char *p = tmp;
+  auto carve = [&](size_t bytes) {
+    char *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  int32_t *row_of = (int32_t *)carve(sizeof(int32_t) * nnz);
+  int32_t *k0 = (int32_t *)carve(sizeof(int32_t) * nnz);
+  int32_t *k1 = (int32_t *)carve(sizeof(int32_t) * nnz);
+  P *p0 = (P *)carve(sizeof(P) * nnz);
+  P *p1 = (P *)carve(sizeof(P) * nnz);
+  int64_t *hist = (int64_t *)carve(sizeof(int64_t) * nh);
+  int64_t *offs = (int64_t *)carve(sizeof(int64_t) * (nh + 1));
+  int64_t *stmp = (int64_t *)carve(sizeof(int64_t) * scan_tmp_len(nh));
+  k_row_of<<<(unsigned)((m + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(row_ptr, m, row_of);
+  cudaMemcpyAsync(k0, col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s);
+  k_iota<P><<<1216, TVR_BLOCK, 0, s>>>(p0, nnz);
+  int bits = 1;
+  while (bits < 31 && ((int64_t)1 << bits) < N) ++bits;
+  const unsigned blocks = (unsigned)((nsub + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<<<blocks, TVR_BLOCK, 0, s>>>(k0, nnz, shift, nsub, hist);
+    cudaError_t e = scan_exclusive_i64(hist, nh, offs, stmp, s);
+    if (e != cudaSuccess) return e;
+    k_radix_scatter<P><<<blocks, TVR_BLOCK, 0, s>>>(k0, p0, nnz, shift, nsub, offs, k1, p1);
+    int32_t *tk = k0; k0 = k1; k1 = tk;
+    P *tp = p0; p0 = p1; p1 = tp;
+  }
+  k_csc_gather<P><<<1216, TVR_BLOCK, 0, s>>>(p0, nnz, row_of, val, row, cval);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// CSC of A: col_ptr from the column counts, rows and values by a stable
+// radix sort of the CSR entries by column.  cnt: N int64; tmp: csc_tmp_bytes.
 cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
                        int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
-                       int64_t *cnt /*N*/, int64_t *key /*nnz*/, int64_t *tmp, cudaStream_t s) {
+                       int64_t *cnt, char *tmp, int64_t *scan_tmp, cudaStream_t s) {
   cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
   if (nnz > 0) k_col_hist<<<1216, TVR_BLOCK, 0, s>>>(col, nnz, cnt);
-  cudaError_t e = scan_exclusive_i64(cnt, N, col_ptr, tmp, s);
-  if (e != cudaSuccess) return e;
-  cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
-  if (m > 0)
-    k_csc_scatter<<<(unsigned)((m + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(
-        row_ptr, col, val, m, col_ptr, cnt, key, row, cval);
-  if (N > 0)
-    k_col_sort<<<(unsigned)((N + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(col_ptr, N, key,
-                                                                                 row, cval);
-  return cudaGetLastError();
+  cudaError_t e = scan_exclusive_i64(cnt, N, col_ptr, scan_tmp, s);
+  if (e != cudaSuccess || nnz == 0) return e;
+  if (nnz >= ((int64_t)1 << 31))
+    return radix_transpose<int64_t>(row_ptr, col, val, m, N, nnz, row, cval, tmp, s);
+  return radix_transpose<int32_t>(row_ptr, col, val, m, N, nnz, row, cval, tmp, s);
 }

@@ -311,9 +311,10 @@ cudaError_t siddon_count(const double *views_dev, int n, int Pu, int Pv, int kin
                          int64_t *counts, cudaStream_t s);
 cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
                         const int64_t *row_ptr, int32_t *cols, float *vals, cudaStream_t s);
+size_t csc_tmp_bytes(int64_t nnz, int64_t N);
 cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
                        int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
-                       int64_t *cnt, int64_t *key, int64_t *tmp, cudaStream_t s);
+                       int64_t *cnt, char *tmp, int64_t *scan_tmp, cudaStream_t s);
 
 int occupancy_grid(const void *kernel, int block, int device);
 void kernel_grids(Workspace &ws, int device);
