@@ -131,6 +131,28 @@ TVR_API int tvr_phi_and_grad(const tvr_system *sys, const float *x, const float 
                      double tau, double *phi_dev, double *phi_host, float *grad,
                      float *resid, void *stream);
 
+/*
+ * tvr_phi_and_grad without any device allocation (the paper has no
+ * counterpart: this serves callers that cannot allocate while they evaluate
+ * phi -- code recording a CUDA stream capture, code whose device memory is
+ * owned by another framework's allocator, real-time loops that must not enter
+ * the driver's allocator).  Same kernels and results as tvr_phi_and_grad
+ * (no resid output).  Its scratch -- the residual and the reduction
+ * partials -- is one fixed device array inside the library (about 16.4 MiB,
+ * held on every GPU that loads the library until the process exits), so:
+ *   - the system's rays m must be <= 4,194,304, else TVR_ERR_ARG;
+ *   - x, b (and grad, phi_dev when given) must be DEVICE memory (host data
+ *     would need staging buffers), else TVR_ERR_ARG;
+ *   - the first call on a device looks up the array's device address; make
+ *     that first call before any stream capture;
+ *   - every call shares the array: calls whose work overlaps on the GPU
+ *     (other streams, other threads) race; order them on one stream.
+ * phi_dev / phi_host as in tvr_phi_and_grad (phi_host synchronises).
+ */
+TVR_API int tvr_phi_and_grad_noalloc(const tvr_system *sys, const float *x, const float *b,
+                                     double alpha, double tau, double *phi_dev,
+                                     double *phi_host, float *grad, void *stream);
+
 /* In place x <- P_Q(x) = max(x, 0) on n DEVICE floats (Sec. III-A); NaN stays NaN. */
 TVR_API int tvr_project_Q(float *x, int64_t n, void *stream);
 
