@@ -25,6 +25,34 @@ int tvr_cuda_fail(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? TVR_ERR_OOM : TVR_ERR_CUDA;
 }
 
+// Copy a padded compressed layout to host and drop the padding entries.
+static int export_compact(const int64_t *ptr_d, const int32_t *len_d, const int32_t *idx_d,
+                          const float *val_d, int64_t rows, int64_t stored, int64_t *ptr_out,
+                          int32_t *idx_out, float *val_out) {
+  std::vector<int64_t> ptr(rows + 1);
+  std::vector<int32_t> len(rows > 0 ? rows : 1);
+  TVR_CUDA(cudaMemcpy(ptr.data(), ptr_d, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost));
+  if (rows > 0)
+    TVR_CUDA(cudaMemcpy(len.data(), len_d, sizeof(int32_t) * rows, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> idx(idx_out && stored ? stored : 0);
+  std::vector<float> val(val_out && stored ? stored : 0);
+  if (!idx.empty())
+    TVR_CUDA(cudaMemcpy(idx.data(), idx_d, sizeof(int32_t) * stored, cudaMemcpyDeviceToHost));
+  if (!val.empty())
+    TVR_CUDA(cudaMemcpy(val.data(), val_d, sizeof(float) * stored, cudaMemcpyDeviceToHost));
+  int64_t o = 0;
+  if (ptr_out) ptr_out[0] = 0;
+  for (int64_t i = 0; i < rows; ++i) {
+    for (int32_t k = 0; k < len[i]; ++k) {
+      if (idx_out) idx_out[o + k] = idx[ptr[i] + k];
+      if (val_out) val_out[o + k] = val[ptr[i] + k];
+    }
+    o += len[i];
+    if (ptr_out) ptr_out[i + 1] = o;
+  }
+  return TVR_OK;
+}
+
 extern "C" {
 
 const char *tvr_status_str(int status) {
@@ -53,9 +81,9 @@ int tvr_system_free(tvr_system *sys) {
     for (int i = 0; i < kProfPairs; ++i)
       for (int w = 0; w < 2; ++w)
         if (sys->prof_ev[k][i][w]) cudaEventDestroy(sys->prof_ev[k][i][w]);
-  void *ptrs[] = {sys->row_ptr, sys->col_ptr, sys->col, sys->row, sys->val, sys->cval,
-                  sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
-                  sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev};
+  free_matrix(sys->A);
+  void *ptrs[] = {sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
+                  sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev, sys->t2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (float *p : sys->vN)
@@ -84,14 +112,8 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   tvr_system *sys = new tvr_system();
   int rc = TVR_OK;
   double *views_dev = nullptr;
-  int64_t *counts = nullptr, *tmp = nullptr, *ccnt = nullptr;
-  char *key = nullptr;
   auto cleanup = [&]() {
     if (views_dev) cudaFree(views_dev);
-    if (counts) cudaFree(counts);
-    if (tmp) cudaFree(tmp);
-    if (key) cudaFree(key);
-    if (ccnt) cudaFree(ccnt);
   };
 #define BUILD_CUDA(call)                          \
   do {                                            \
@@ -115,28 +137,8 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   const size_t vbytes = sizeof(double) * TVR_VIEW_FIELDS * g->n_views;
   BUILD_CUDA(cudaMalloc(&views_dev, vbytes));
   BUILD_CUDA(cudaMemcpyAsync(views_dev, g->views, vbytes, cudaMemcpyHostToDevice, s));
-  BUILD_CUDA(cudaMalloc(&counts, sizeof(int64_t) * m));
-  const int64_t tl = scan_tmp_len(m > N ? m : N);
-  BUILD_CUDA(cudaMalloc(&tmp, sizeof(int64_t) * tl));
-  BUILD_CUDA(cudaMalloc(&sys->row_ptr, sizeof(int64_t) * (m + 1)));
-  BUILD_CUDA(siddon_count(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, counts, s));
-  BUILD_CUDA(scan_exclusive_i64(counts, m, sys->row_ptr, tmp, s));
-  int64_t nnz = 0;
-  BUILD_CUDA(cudaMemcpyAsync(&nnz, sys->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  BUILD_CUDA(cudaStreamSynchronize(s));
-  sys->nnz = nnz;
-  const int64_t nz1 = nnz > 0 ? nnz : 1;
-  BUILD_CUDA(cudaMalloc(&sys->col, sizeof(int32_t) * nz1));
-  BUILD_CUDA(cudaMalloc(&sys->val, sizeof(float) * nz1));
-  BUILD_CUDA(siddon_fill(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, sys->row_ptr,
-                         sys->col, sys->val, s));
-  BUILD_CUDA(cudaMalloc(&sys->col_ptr, sizeof(int64_t) * (N + 1)));
-  BUILD_CUDA(cudaMalloc(&sys->row, sizeof(int32_t) * nz1));
-  BUILD_CUDA(cudaMalloc(&sys->cval, sizeof(float) * nz1));
-  BUILD_CUDA(cudaMalloc(&key, csc_tmp_bytes(nnz, N)));
-  BUILD_CUDA(cudaMalloc(&ccnt, sizeof(int64_t) * N));
-  BUILD_CUDA(csr_to_csc(sys->row_ptr, sys->col, sys->val, m, N, nnz, sys->col_ptr, sys->row,
-                        sys->cval, ccnt, key, tmp, s));
+  BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
+  sys->nnz = sys->A.nnz;
   // reduction workspace: per slot partials + counter + outputs
   const size_t part = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;
   const size_t slot_bytes = part + 256 + 256;
@@ -172,26 +174,16 @@ int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col,
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
-  if (row_ptr)
-    TVR_CUDA(cudaMemcpy(row_ptr, sys->row_ptr, sizeof(int64_t) * (sys->m + 1), cudaMemcpyDeviceToHost));
-  if (col && sys->nnz)
-    TVR_CUDA(cudaMemcpy(col, sys->col, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
-  if (val && sys->nnz)
-    TVR_CUDA(cudaMemcpy(val, sys->val, sizeof(float) * sys->nnz, cudaMemcpyDeviceToHost));
-  return TVR_OK;
+  return export_compact(sys->A.row_ptr, sys->A.row_len, sys->A.col, sys->A.val, sys->m,
+                        sys->A.nnz_pad, row_ptr, col, val);
 }
 
 int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val) {
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
-  if (col_ptr)
-    TVR_CUDA(cudaMemcpy(col_ptr, sys->col_ptr, sizeof(int64_t) * (sys->N + 1), cudaMemcpyDeviceToHost));
-  if (row && sys->nnz)
-    TVR_CUDA(cudaMemcpy(row, sys->row, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
-  if (val && sys->nnz)
-    TVR_CUDA(cudaMemcpy(val, sys->cval, sizeof(float) * sys->nnz, cudaMemcpyDeviceToHost));
-  return TVR_OK;
+  return export_compact(sys->A.col_ptr, sys->A.col_len, sys->A.row, sys->A.cval, sys->N,
+                        sys->A.nnz_cpad, col_ptr, row, val);
 }
 
 int tvr_forward(const tvr_system *csys, const float *x, float *y, void *stream) {

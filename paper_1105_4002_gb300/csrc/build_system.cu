@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "tvr_internal.cuh"
 
 namespace {
@@ -159,7 +161,23 @@ __global__ void k_siddon_fill(const ViewRec *__restrict__ views, int n, int Pu, 
   double s[3], c[3];
   endpoints(views[v].v, kind, Pu, Pv, p, q, s, c);
   const int64_t o = row_ptr[i];
-  trace<true>(s, c, n, cols + o, vals + o);
+  const int len = trace<true>(s, c, n, cols + o, vals + o);
+  // padding up to the next multiple of 4: last real voxel, length 0
+  const int64_t padded = row_ptr[i + 1] - o;
+  for (int64_t k = len; k < padded; ++k) {
+    cols[o + k] = len > 0 ? cols[o + len - 1] : 0;
+    vals[o + k] = 0.f;
+  }
+}
+
+// padded[i] = count rounded up to a multiple of 4; len[i] = count.
+__global__ void k_pad4(const int64_t *__restrict__ cnt, int64_t n, int64_t *__restrict__ padded,
+                       int32_t *__restrict__ len) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t c = cnt[i];
+  padded[i] = (c + 3) & ~(int64_t)3;
+  len[i] = (int32_t)c;
 }
 
 // ---- exclusive scan of int64 counts: out[0] = 0, out[i+1] = sum(in[0..i]) ----
@@ -244,16 +262,29 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 constexpr int kSubItems = 8192;                 // entries per warp range
 constexpr int kWarpsPerBlock = TVR_BLOCK / 32;  // 8
 
-__global__ void k_col_hist(const int32_t *__restrict__ col, int64_t nnz, int64_t *__restrict__ cnt) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
-    atomicAdd(reinterpret_cast<unsigned long long *>(cnt + col[e]), 1ull);
-}
-
-__global__ void k_row_of(const int64_t *__restrict__ row_ptr, int64_t m, int32_t *__restrict__ row_of) {
+// Column counts of the real (non-padding) entries.
+__global__ void k_col_hist(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ row_len,
+                           const int32_t *__restrict__ col, int64_t m, int64_t *__restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) row_of[e] = (int32_t)i;
+  const int64_t o = row_ptr[i];
+  for (int k = 0; k < row_len[i]; ++k)
+    atomicAdd(reinterpret_cast<unsigned long long *>(cnt + col[o + k]), 1ull);
+}
+
+// Sort keys (the column; N for padding, so padding sorts last) and the row of
+// every stored CSR entry.
+__global__ void k_radix_keys(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ row_len,
+                             const int32_t *__restrict__ col, int64_t m, int32_t N,
+                             int32_t *__restrict__ key, int32_t *__restrict__ row_of) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t o = row_ptr[i], end = row_ptr[i + 1];
+  const int len = row_len[i];
+  for (int64_t e = o; e < end; ++e) {
+    key[e] = e - o < len ? col[e] : N;
+    row_of[e] = (int32_t)i;
+  }
 }
 
 template <typename P>
@@ -313,15 +344,24 @@ __global__ void k_radix_scatter(const int32_t *__restrict__ key_in, const P *__r
   }
 }
 
+// Column c's entries (sorted positions [cu[c], cu[c+1])) to the padded CSC
+// at cp[c], then padding: last real row, value 0.
 template <typename P>
-__global__ void k_csc_gather(const P *__restrict__ perm, int64_t nnz, const int32_t *__restrict__ row_of,
-                             const float *__restrict__ val, int32_t *__restrict__ row,
-                             float *__restrict__ cval) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
-    const int64_t e = (int64_t)perm[k];
-    row[k] = row_of[e];
-    cval[k] = val[e];
+__global__ void k_csc_place(const int64_t *__restrict__ cu, const int64_t *__restrict__ cp,
+                            const P *__restrict__ perm, const int32_t *__restrict__ row_of,
+                            const float *__restrict__ val, int64_t N, int32_t *__restrict__ row,
+                            float *__restrict__ cval) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const int64_t u0 = cu[c], len = cu[c + 1] - u0, o = cp[c], padded = cp[c + 1] - o;
+  for (int64_t k = 0; k < len; ++k) {
+    const int64_t e = (int64_t)perm[u0 + k];
+    row[o + k] = row_of[e];
+    cval[o + k] = val[e];
+  }
+  for (int64_t k = len; k < padded; ++k) {
+    row[o + k] = len > 0 ? row[o + len - 1] : 0;
+    cval[o + k] = 0.f;
   }
 }
 
@@ -343,82 +383,133 @@ cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64
 
 int64_t scan_tmp_len(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-cudaError_t siddon_count(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
-                         int64_t *counts, cudaStream_t s) {
-  const unsigned grid = (unsigned)((m + 127) / 128);
-  k_siddon_count<<<grid, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv, kind,
-                                      m, counts);
-  return cudaGetLastError();
-}
-
-cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
-                        const int64_t *row_ptr, int32_t *cols, float *vals, cudaStream_t s) {
-  const unsigned grid = (unsigned)((m + 127) / 128);
-  k_siddon_fill<<<grid, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv, kind,
-                                     m, row_ptr, cols, vals);
-  return cudaGetLastError();
-}
-
-// Bytes of temporary device memory csr_to_csc needs.
-size_t csc_tmp_bytes(int64_t nnz, int64_t N) {
-  const size_t pay = nnz >= ((int64_t)1 << 31) ? 8 : 4;
-  const int64_t nsub = (nnz + kSubItems - 1) / kSubItems;
-  const int64_t nh = 256 * (nsub > 0 ? nsub : 1);
-  return (size_t)nnz * (4 + 4 + 4 + 2 * pay) + sizeof(int64_t) * (2 * nh + scan_tmp_len(nh) + N) + 4096;
-}
-
 namespace {
 
+struct Scratch {
+  std::vector<void *> ptrs;
+  ~Scratch() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T **out, int64_t count) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)(count > 0 ? count : 1));
+    if (e == cudaSuccess) ptrs.push_back(p);
+    *out = static_cast<T *>(p);
+    return e;
+  }
+};
+
+#define BM_TRY(call)                        \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+
+template <typename T>
+cudaError_t owned(T **out, int64_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(out), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)((n + TVR_BLOCK - 1) / TVR_BLOCK); }
+
+// Stable radix sort of the padded CSR entries by column (padding last); then
+// placement into the padded CSC.
 template <typename P>
-cudaError_t radix_transpose(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
-                            int64_t N, int64_t nnz, int32_t *row, float *cval, char *tmp,
-                            cudaStream_t s) {
-  const int64_t nsub = (nnz + kSubItems - 1) / kSubItems;
+cudaError_t transpose(MatStore &A, cudaStream_t s) {
+  Scratch t;
+  const int64_t n = A.nnz_pad, N = A.N, m = A.m;
+  const int64_t nsub = (n + kSubItems - 1) / kSubItems;
   const int64_t nh = 256 * nsub;
-  char *p = tmp;
-  auto carve = [&](size_t bytes) {
-    char *q = p;
-    p += (bytes + 255) / 256 * 256;
-    return q;
-  };
-  int32_t *row_of = (int32_t *)carve(sizeof(int32_t) * nnz);
-  int32_t *k0 = (int32_t *)carve(sizeof(int32_t) * nnz);
-  int32_t *k1 = (int32_t *)carve(sizeof(int32_t) * nnz);
-  P *p0 = (P *)carve(sizeof(P) * nnz);
-  P *p1 = (P *)carve(sizeof(P) * nnz);
-  int64_t *hist = (int64_t *)carve(sizeof(int64_t) * nh);
-  int64_t *offs = (int64_t *)carve(sizeof(int64_t) * (nh + 1));
-  int64_t *stmp = (int64_t *)carve(sizeof(int64_t) * scan_tmp_len(nh));
-  k_row_of<<<(unsigned)((m + TVR_BLOCK - 1) / TVR_BLOCK), TVR_BLOCK, 0, s>>>(row_ptr, m, row_of);
-  cudaMemcpyAsync(k0, col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s);
-  k_iota<P><<<1216, TVR_BLOCK, 0, s>>>(p0, nnz);
+  int32_t *row_of, *k0, *k1;
+  P *p0, *p1;
+  int64_t *hist, *offs, *stmp, *cu, *cnt;
+  BM_TRY(t.get(&row_of, n));
+  BM_TRY(t.get(&k0, n));
+  BM_TRY(t.get(&k1, n));
+  BM_TRY(t.get(&p0, n));
+  BM_TRY(t.get(&p1, n));
+  BM_TRY(t.get(&hist, nh));
+  BM_TRY(t.get(&offs, nh + 1));
+  BM_TRY(t.get(&stmp, scan_tmp_len(nh > N ? nh : N)));
+  BM_TRY(t.get(&cu, N + 1));
+  BM_TRY(t.get(&cnt, N));
+  // unpadded column offsets (positions of each column in the sorted order)
+  BM_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s));
+  k_col_hist<<<blocks_for(m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, A.col, m, cnt);
+  BM_TRY(scan_exclusive_i64(cnt, N, cu, stmp, s));
+  k_radix_keys<<<blocks_for(m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, A.col, m, (int32_t)N, k0,
+                                                    row_of);
+  k_iota<P><<<1216, TVR_BLOCK, 0, s>>>(p0, n);
   int bits = 1;
-  while (bits < 31 && ((int64_t)1 << bits) < N) ++bits;
+  while (bits < 31 && ((int64_t)1 << bits) <= N) ++bits;  // keys 0..N
   const unsigned blocks = (unsigned)((nsub + kWarpsPerBlock - 1) / kWarpsPerBlock);
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<blocks, TVR_BLOCK, 0, s>>>(k0, nnz, shift, nsub, hist);
-    cudaError_t e = scan_exclusive_i64(hist, nh, offs, stmp, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<P><<<blocks, TVR_BLOCK, 0, s>>>(k0, p0, nnz, shift, nsub, offs, k1, p1);
+    k_radix_hist<<<blocks, TVR_BLOCK, 0, s>>>(k0, n, shift, nsub, hist);
+    BM_TRY(scan_exclusive_i64(hist, nh, offs, stmp, s));
+    k_radix_scatter<P><<<blocks, TVR_BLOCK, 0, s>>>(k0, p0, n, shift, nsub, offs, k1, p1);
     int32_t *tk = k0; k0 = k1; k1 = tk;
     P *tp = p0; p0 = p1; p1 = tp;
   }
-  k_csc_gather<P><<<1216, TVR_BLOCK, 0, s>>>(p0, nnz, row_of, val, row, cval);
-  return cudaGetLastError();
+  k_csc_place<P><<<blocks_for(N), TVR_BLOCK, 0, s>>>(cu, A.col_ptr, p0, row_of, A.val, N, A.row,
+                                                      A.cval);
+  BM_TRY(cudaGetLastError());
+  return cudaStreamSynchronize(s);  // scratch is freed on return
 }
 
 }  // namespace
 
-// CSC of A: col_ptr from the column counts, rows and values by a stable
-// radix sort of the CSR entries by column.  cnt: N int64; tmp: csc_tmp_bytes.
-cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
-                       int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
-                       int64_t *cnt, char *tmp, int64_t *scan_tmp, cudaStream_t s) {
-  cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
-  if (nnz > 0) k_col_hist<<<1216, TVR_BLOCK, 0, s>>>(col, nnz, cnt);
-  cudaError_t e = scan_exclusive_i64(cnt, N, col_ptr, scan_tmp, s);
-  if (e != cudaSuccess || nnz == 0) return e;
-  if (nnz >= ((int64_t)1 << 31))
-    return radix_transpose<int64_t>(row_ptr, col, val, m, N, nnz, row, cval, tmp, s);
-  return radix_transpose<int32_t>(row_ptr, col, val, m, N, nnz, row, cval, tmp, s);
+void free_matrix(MatStore &A) {
+  void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col, A.row, A.val, A.cval};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  A = MatStore{};
+}
+
+// A for one scan: Siddon counts -> rows padded to multiples of 4 -> fill ->
+// padded CSC.  Synchronises `s` (sizes are read back twice).  On failure the
+// partially built arrays stay in A for free_matrix.
+cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                         int64_t N, MatStore &A, cudaStream_t s) {
+  A = MatStore{};
+  A.m = m;
+  A.N = N;
+  Scratch t;
+  int64_t *counts, *padded, *tmp, *rp_real, *ccnt, *cpad;
+  BM_TRY(t.get(&counts, m));
+  BM_TRY(t.get(&padded, m > N ? m : N));
+  BM_TRY(t.get(&tmp, scan_tmp_len(m > N ? m : N)));
+  BM_TRY(t.get(&rp_real, m + 1));
+  BM_TRY(owned(&A.row_ptr, m + 1));
+  BM_TRY(owned(&A.row_len, m));
+  const unsigned rays = (unsigned)((m + 127) / 128);
+  k_siddon_count<<<rays, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv,
+                                      kind, m, counts);
+  k_pad4<<<blocks_for(m), TVR_BLOCK, 0, s>>>(counts, m, padded, A.row_len);
+  BM_TRY(scan_exclusive_i64(padded, m, A.row_ptr, tmp, s));
+  BM_TRY(scan_exclusive_i64(counts, m, rp_real, tmp, s));
+  BM_TRY(cudaMemcpyAsync(&A.nnz_pad, A.row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BM_TRY(cudaMemcpyAsync(&A.nnz, rp_real + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BM_TRY(cudaStreamSynchronize(s));
+  BM_TRY(owned(&A.col, A.nnz_pad));
+  BM_TRY(owned(&A.val, A.nnz_pad));
+  k_siddon_fill<<<rays, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), n, Pu, Pv, kind,
+                                     m, A.row_ptr, A.col, A.val);
+  // column counts -> padded column pointers
+  BM_TRY(t.get(&ccnt, N));
+  BM_TRY(t.get(&cpad, N));
+  BM_TRY(owned(&A.col_ptr, N + 1));
+  BM_TRY(owned(&A.col_len, N));
+  BM_TRY(cudaMemsetAsync(ccnt, 0, sizeof(int64_t) * N, s));
+  k_col_hist<<<blocks_for(m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, A.col, m, ccnt);
+  k_pad4<<<blocks_for(N), TVR_BLOCK, 0, s>>>(ccnt, N, cpad, A.col_len);
+  BM_TRY(scan_exclusive_i64(cpad, N, A.col_ptr, tmp, s));
+  BM_TRY(cudaMemcpyAsync(&A.nnz_cpad, A.col_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BM_TRY(cudaStreamSynchronize(s));
+  BM_TRY(owned(&A.row, A.nnz_cpad));
+  BM_TRY(owned(&A.cval, A.nnz_cpad));
+  BM_TRY(cudaGetLastError());
+  if (A.nnz_pad == 0) return cudaStreamSynchronize(s);
+  if (A.nnz_pad >= ((int64_t)1 << 31)) return transpose<int64_t>(A, s);
+  return transpose<int32_t>(A, s);
 }

@@ -18,8 +18,30 @@
 
 namespace {
 
-constexpr int kRowLanes = 8;  // lanes per CSR row
-constexpr int kColLanes = 8;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
+#ifndef TVR_ROW_LANES
+#define TVR_ROW_LANES 4
+#endif
+#ifndef TVR_COL_LANES
+#define TVR_COL_LANES 4
+#endif
+#ifndef TVR_FWD_MIN_BLOCKS
+#define TVR_FWD_MIN_BLOCKS 5
+#endif
+#ifndef TVR_BWD_MIN_BLOCKS
+#define TVR_BWD_MIN_BLOCKS 5
+#endif
+#ifndef TVR_ROW_CHUNKS
+#define TVR_ROW_CHUNKS 2
+#endif
+#ifndef TVR_COL_CHUNKS
+#define TVR_COL_CHUNKS 2
+#endif
+constexpr int kRowChunks = TVR_ROW_CHUNKS;  // 4-entry chunks per lane per loop trip (CSR)
+constexpr int kColChunks = TVR_COL_CHUNKS;  // same for the CSC loop
+constexpr int kRowLanes = TVR_ROW_LANES;  // lanes per CSR row
+constexpr int kColLanes = TVR_COL_LANES;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
+static_assert(kColLanes >= 4 && kColLanes <= 32 && (kColLanes & (kColLanes - 1)) == 0, "lanes");
+static_assert(kRowLanes >= 1 && kRowLanes <= 32 && (kRowLanes & (kRowLanes - 1)) == 0, "lanes");
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v) {
@@ -38,11 +60,11 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3 };
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
 template <int G, int MODE>
-__global__ void __launch_bounds__(TVR_BLOCK)
+__global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
               float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1) {
   const float *x = xin;
-  const float *p = nullptr;
+  const float2 *xd = nullptr;  // trial mode: (xbar, xbar - base) per voxel
   float *r = rout;
   float *ad = nullptr;
   if (MODE == FWD_INIT) {
@@ -55,8 +77,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
     if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->prof_flags[prof_slot] = 1;
     const bool upn = st->solver == SOLVER_UPN;
     b = st->b;
-    x = st->vN[RN_T];
-    p = upn ? st->vN[RN_Y] : st->vN[RN_X];
+    xd = st->t2;
     r = st->vM[RM_RT];
     ad = upn ? st->vM[RM_AD] : nullptr;
   }
@@ -75,12 +96,47 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       end = __ldg(A.row_ptr + row + 1);
     }
     float sx = 0.f, sd = 0.f;
-    for (int64_t e = beg + lane; e < end; e += G) {
-      const int c = __ldg(A.col + e);
-      const float v = __ldg(A.val + e);
-      const float xv = __ldg(x + c);
-      sx = __fmaf_rn(v, xv, sx);
-      if (MODE == FWD_TRIAL) sd = __fmaf_rn(v, __fsub_rn(xv, __ldg(p + c)), sd);
+    // Rows are padded to multiples of 4 entries: each lane reads 4 entries
+    // with one 16-byte load of indices and one of values, then gathers.
+    // Trial mode gathers (xbar_j, xbar_j - p_j) pairs with one 8-byte load.
+    for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kRowChunks) {
+      // all index / value loads of this trip first, then the gathers
+      int4 c4[kRowChunks];
+      float4 v4[kRowChunks];
+#pragma unroll
+      for (int u = 0; u < kRowChunks; ++u) {
+        const int64_t e = e0 + (int64_t)u * 4 * G;
+        if (e < end) {
+          c4[u] = __ldg(reinterpret_cast<const int4 *>(A.col + e));
+          v4[u] = __ldg(reinterpret_cast<const float4 *>(A.val + e));
+        } else {
+          c4[u] = make_int4(0, 0, 0, 0);
+          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kRowChunks; ++u) {
+        if (e0 + (int64_t)u * 4 * G >= end) break;
+        if (MODE == FWD_TRIAL) {
+          const float2 t0 = __ldg(xd + c4[u].x), t1 = __ldg(xd + c4[u].y);
+          const float2 t2 = __ldg(xd + c4[u].z), t3 = __ldg(xd + c4[u].w);
+          sx = __fmaf_rn(v4[u].x, t0.x, sx);
+          sd = __fmaf_rn(v4[u].x, t0.y, sd);
+          sx = __fmaf_rn(v4[u].y, t1.x, sx);
+          sd = __fmaf_rn(v4[u].y, t1.y, sd);
+          sx = __fmaf_rn(v4[u].z, t2.x, sx);
+          sd = __fmaf_rn(v4[u].z, t2.y, sd);
+          sx = __fmaf_rn(v4[u].w, t3.x, sx);
+          sd = __fmaf_rn(v4[u].w, t3.y, sd);
+        } else {
+          const float x0 = __ldg(x + c4[u].x), x1 = __ldg(x + c4[u].y);
+          const float x2 = __ldg(x + c4[u].z), x3 = __ldg(x + c4[u].w);
+          sx = __fmaf_rn(v4[u].x, x0, sx);
+          sx = __fmaf_rn(v4[u].y, x1, sx);
+          sx = __fmaf_rn(v4[u].z, x2, sx);
+          sx = __fmaf_rn(v4[u].w, x3, sx);
+        }
+      }
     }
     sx = group_sum<G>(sx);
     if (MODE == FWD_TRIAL) sd = group_sum<G>(sd);
@@ -117,7 +173,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
 // j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
 // ---------------------------------------------------------------------------
 template <int G, int MODE>
-__global__ void __launch_bounds__(TVR_BLOCK)
+__global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
                const double *__restrict__ data_in, double *phi_dev, DevState *st,
@@ -169,9 +225,30 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       end = __ldg(A.col_ptr + j + 1);
     }
     float s = 0.f;
-    for (int64_t e = beg + lane; e < end; e += G) {
-      const int i = __ldg(A.row + e);
-      s = __fmaf_rn(__ldg(A.cval + e), __ldg(r + i), s);
+    for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kColChunks) {
+      int4 i4[kColChunks];
+      float4 v4[kColChunks];
+#pragma unroll
+      for (int u = 0; u < kColChunks; ++u) {
+        const int64_t e = e0 + (int64_t)u * 4 * G;
+        if (e < end) {
+          i4[u] = __ldg(reinterpret_cast<const int4 *>(A.row + e));
+          v4[u] = __ldg(reinterpret_cast<const float4 *>(A.cval + e));
+        } else {
+          i4[u] = make_int4(0, 0, 0, 0);
+          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kColChunks; ++u) {
+        if (e0 + (int64_t)u * 4 * G >= end) break;
+        const float r0 = __ldg(r + i4[u].x), r1 = __ldg(r + i4[u].y);
+        const float r2 = __ldg(r + i4[u].z), r3 = __ldg(r + i4[u].w);
+        s = __fmaf_rn(v4[u].x, r0, s);
+        s = __fmaf_rn(v4[u].y, r1, s);
+        s = __fmaf_rn(v4[u].z, r2, s);
+        s = __fmaf_rn(v4[u].w, r3, s);
+      }
     }
     s = group_sum<G>(s);
     if (MODE == BWD_ADJ) {
@@ -185,7 +262,8 @@ __global__ void __launch_bounds__(TVR_BLOCK)
     float c = 0.f;
     if (valid && lane < 4) {
       huber_at(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, hw);
-      c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2]) : hw.w[lane - 1];
+      c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2])
+                    : (lane == 1 ? hw.w[0] : (lane == 2 ? hw.w[1] : hw.w[2]));
     }
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 2, G));
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 1, G));
@@ -243,6 +321,7 @@ __global__ void __launch_bounds__(TVR_BLOCK) k_step(MatDev A, RedSlot slot, DevS
   const float *__restrict__ p = upn ? st->vN[RN_Y] : st->vN[RN_X];
   const float *__restrict__ g = st->vN[RN_G];
   float *__restrict__ t = st->vN[RN_T];
+  float2 *__restrict__ t2 = st->t2;
   const float s = (float)st->step;
   const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
   const float s2 = (float)st->step2;
@@ -256,6 +335,7 @@ __global__ void __launch_bounds__(TVR_BLOCK) k_step(MatDev A, RedSlot slot, DevS
     const float xb = proj(__fsub_rn(pj, __fmul_rn(s, gj)));
     t[j] = xb;
     const float d = __fsub_rn(xb, pj);
+    t2[j] = make_float2(xb, d);
     ff_add_prod(a0, gj, d);
     ff_add_prod(a1, d, d);
     if (want_g2) {

@@ -24,6 +24,7 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
     if (int rc = ensure_vec(&p, sys->N)) return rc;
   for (auto &p : sys->vM)
     if (int rc = ensure_vec(&p, sys->m)) return rc;
+  if (!sys->t2) TVR_CUDA(cudaMalloc(&sys->t2, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));
   if (!sys->st) TVR_CUDA(cudaMalloc(&sys->st, sizeof(DevState)));
   if (!sys->pinned_flag) TVR_CUDA(cudaMallocHost(&sys->pinned_flag, 64));
   if (!sys->cap_stream) TVR_CUDA(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking));
@@ -114,6 +115,7 @@ int solve(const tvr_system *csys, int solver, const float *b, double alpha, doub
   h.b = bd;
   for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
   for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
+  h.t2 = sys->t2;
   h.hist = hist_n > 0 ? sys->hist_dev : nullptr;
   h.prof_flags = sys->prof_flags_dev;
   h.hist_cap = (int)hist_n;

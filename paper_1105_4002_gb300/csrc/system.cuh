@@ -23,9 +23,7 @@ struct tvr_system {
   int device = 0;
   int n = 0, V = 0, Pu = 0, Pv = 0, kind = 0;
   int64_t m = 0, N = 0, nnz = 0;
-  int64_t *row_ptr = nullptr, *col_ptr = nullptr;
-  int32_t *col = nullptr, *row = nullptr;
-  float *val = nullptr, *cval = nullptr;
+  MatStore A;  // padded CSR + CSC
   void *ws_mem = nullptr;
   Workspace ws{};
   // staging and scratch vectors (allocated on first use)
@@ -35,6 +33,7 @@ struct tvr_system {
   DevState *st = nullptr;
   float *vN[RN_COUNT] = {};
   float *vM[RM_COUNT] = {};
+  float2 *t2 = nullptr;
   double *hist_dev = nullptr;
   int hist_cap = 0;
   int *pinned_flag = nullptr;
@@ -53,18 +52,18 @@ struct tvr_system {
   int64_t prof_cnt[2] = {0, 0};
 
   MatDev mat() const {
-    MatDev A;
-    A.n = n;
-    A.m = m;
-    A.N = N;
-    A.nnz = nnz;
-    A.row_ptr = row_ptr;
-    A.col = col;
-    A.val = val;
-    A.col_ptr = col_ptr;
-    A.row = row;
-    A.cval = cval;
-    return A;
+    MatDev d;
+    d.n = n;
+    d.m = m;
+    d.N = N;
+    d.nnz = A.nnz_pad;
+    d.row_ptr = A.row_ptr;
+    d.col = A.col;
+    d.val = A.val;
+    d.col_ptr = A.col_ptr;
+    d.row = A.row;
+    d.cval = A.cval;
+    return d;
   }
 };
 

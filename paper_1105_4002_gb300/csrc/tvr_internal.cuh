@@ -248,6 +248,7 @@ struct DevState {
   // vector roles
   float *vN[RN_COUNT];
   float *vM[RM_COUNT];
+  float2 *t2;  // trial point and step interleaved: (xbar_j, xbar_j - base_j)
   // history (device buffer of hist_cap records)
   double *hist;
   int hist_cap, hist_used;
@@ -262,12 +263,12 @@ struct DevState {
 struct MatDev {
   int n;
   int64_t m, N, nnz;
-  const int64_t *row_ptr;  // CSR [m+1]
-  const int32_t *col;      // [nnz]
-  const float *val;        // [nnz]
-  const int64_t *col_ptr;  // CSC [N+1]
-  const int32_t *row;      // [nnz]
-  const float *cval;       // [nnz]
+  const int64_t *row_ptr;  // CSR [m+1], every row padded to a multiple of 4 entries
+  const int32_t *col;      // [stored]
+  const float *val;        // [stored]
+  const int64_t *col_ptr;  // CSC [N+1], every column padded to a multiple of 4 entries
+  const int32_t *row;      // [stored]
+  const float *cval;       // [stored]
 };
 
 struct Workspace {
@@ -303,18 +304,26 @@ struct PassTiming {
 void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
                         cudaStream_t s, const PassTiming *timing = nullptr);
 
-// Construction of A (build_system.cu).
+// Construction of A (build_system.cu).  Rows of the CSR and columns of the
+// CSC are padded to multiples of 4 entries (padding: the last real index with
+// value 0) so that every lane reads 4 entries with one 16-byte load; row_len /
+// col_len keep the real counts.
+struct MatStore {
+  int64_t m = 0, N = 0;
+  int64_t nnz = 0;       // real entries
+  int64_t nnz_pad = 0;   // stored CSR entries
+  int64_t nnz_cpad = 0;  // stored CSC entries
+  int64_t *row_ptr = nullptr, *col_ptr = nullptr;  // padded offsets [m+1], [N+1]
+  int32_t *row_len = nullptr, *col_len = nullptr;  // real counts [m], [N]
+  int32_t *col = nullptr, *row = nullptr;
+  float *val = nullptr, *cval = nullptr;
+};
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
                                cudaStream_t s);
 int64_t scan_tmp_len(int64_t n);
-cudaError_t siddon_count(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
-                         int64_t *counts, cudaStream_t s);
-cudaError_t siddon_fill(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
-                        const int64_t *row_ptr, int32_t *cols, float *vals, cudaStream_t s);
-size_t csc_tmp_bytes(int64_t nnz, int64_t N);
-cudaError_t csr_to_csc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t m,
-                       int64_t N, int64_t nnz, int64_t *col_ptr, int32_t *row, float *cval,
-                       int64_t *cnt, char *tmp, int64_t *scan_tmp, cudaStream_t s);
+cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
+                         int64_t N, MatStore &A, cudaStream_t s);
+void free_matrix(MatStore &A);
 
 int occupancy_grid(const void *kernel, int block, int device);
 void kernel_grids(Workspace &ws, int device);
