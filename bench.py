@@ -52,6 +52,8 @@ def parse():
                     help="1: replay passes as CUDA graphs (no per-kernel timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phi-loop", type=int, default=200)
+    ap.add_argument("--pattern", default="solve", choices=["solve", "autograd"],
+                    help="autograd: phi forward + backward through torch.autograd at 128^3")
     return ap.parse_args()
 
 
@@ -212,6 +214,80 @@ def cpu_baseline(cfg, eps, b_host, geom):
                       f"({g} gradient evaluations in {dt:.1f} s, FP64 numpy/scipy, one thread)"}
 
 
+# ------------------------------------------------------------- autograd
+def run_autograd(args):
+    """phi(x; b) forward + backward (torch.autograd) on the 128^3 / 60-view / 192^2 problem."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    from paper_1105_4002_gb300.autograd import phi
+    cfg = synth.get_config("c128")
+    geom = cfg.geometry()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    sysm = tvr.System(geom)
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    xt = torch.tensor(cfg.phantom(), dtype=torch.float32, device=dev)
+    ax = torch.empty(geom.m, dtype=torch.float32, device=dev)
+    sysm.forward(xt, ax)
+    axh = ax.cpu().numpy().astype(np.float64)
+    z = synth.standard_normal(geom.m, cfg.seed + 1000)
+    b = torch.tensor((axh + cfg.noise * np.linalg.norm(axh) / math.sqrt(geom.m) * z)
+                     .astype(np.float32), device=dev, requires_grad=True)
+    x = torch.rand(geom.N, device=dev, requires_grad=True)
+
+    def step():
+        x.grad = None
+        b.grad = None
+        phi(x, b, sysm, cfg.alpha, cfg.tau).backward()
+
+    for _ in range(args.warmup):
+        step()
+    sysm.profile(True)
+    sysm.profile_read()
+    sampler = ClockSampler(gpu_id_for(torch, dev))
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = sysm.profile_read()
+    sysm.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    m, N, nnz = geom.m, geom.N, sysm.nnz
+    bytes_f = 8 * nnz + 8 * (m + 1) + 4 * N + 8 * m
+    bytes_b = 8 * nnz + 8 * (N + 1) + 8 * N + 8 * m
+    (nf, msf), (nb, msb) = prof["forward"], prof["backward"]
+    peak, src = measured_peak_gbs()
+    name, mst, cnt, by = max([("fwd_csr", msf, nf, bytes_f), ("vjp_csc_tv", msb, nb, bytes_b)],
+                             key=lambda c: c[1])
+    ach = by / (mst / cnt / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "phi forward+backward (autograd) evals/s at 128^3", "value": 1e3 / ms,
+        "unit": "fwd+bwd/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "TV-CT 128^3, cone beam 60 views x 192^2 px, 20 ellipsoids, 0.5% noise; "
+                               "phi(x; b) forward and backward through torch.autograd",
+                   "nnz": nnz, "build_system_ms": build_ms,
+                   "l2": "inputs larger than L2: A = 2 x 3.0 GB"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "traffic": None, "kernel": name,
+                     "avg_us": 1e3 * mst / cnt, "peak_source": src,
+                     "fwd_us": 1e3 * msf / max(nf, 1), "bwd_us": 1e3 * msb / max(nb, 1)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -225,6 +301,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, cfg, eps)
+        return
+    if args.pattern == "autograd":
+        if rank == 0:
+            run_autograd(args)
         return
 
     import numpy as np

@@ -132,6 +132,32 @@ TVR_API int tvr_phi_and_grad(const tvr_system *sys, const float *x, const float 
                      float *resid, void *stream);
 
 /*
+ * FP64 variant of tvr_phi_and_grad (eq. TVobjectivefunction) for verification
+ * by finite differences: x, b, grad, resid are DEVICE doubles; A's stored FP32
+ * values are promoted to double, so it is the same function phi in double
+ * arithmetic.  resid (m doubles) and grad (N doubles) are required outputs;
+ * phi_dev / phi_host as in tvr_phi_and_grad.  The reductions are FP64.
+ */
+TVR_API int tvr_phi_and_grad_f64(const tvr_system *sys, const double *x, const double *b,
+                                 double alpha, double tau, double *phi_dev, double *phi_host,
+                                 double *grad, double *resid, void *stream);
+
+/*
+ * Backward of phi(x; b) for reverse-mode differentiation: with the residual
+ * r = A x - b saved by a forward call and the upstream scalar w = *scale_dev
+ * (a DEVICE double),
+ *   grad_x = w (A^T r + alpha grad TV_tau(x)),   grad_b = -w r   (grad_b nullable).
+ * All vectors DEVICE memory; float32 (tvr_phi_vjp) or float64 (tvr_phi_vjp_f64).
+ * Asynchronous on `stream`.
+ */
+TVR_API int tvr_phi_vjp(const tvr_system *sys, const float *x, const float *resid, double alpha,
+                        double tau, const double *scale_dev, float *grad_x, float *grad_b,
+                        void *stream);
+TVR_API int tvr_phi_vjp_f64(const tvr_system *sys, const double *x, const double *resid,
+                            double alpha, double tau, const double *scale_dev, double *grad_x,
+                            double *grad_b, void *stream);
+
+/*
  * tvr_phi_and_grad without any device allocation (the paper has no
  * counterpart: this serves callers that cannot allocate while they evaluate
  * phi -- code recording a CUDA stream capture, code whose device memory is

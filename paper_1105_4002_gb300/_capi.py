@@ -63,6 +63,9 @@ SIGNATURES = {
     "tvr_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "tvr_phi_and_grad": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
     "tvr_phi_and_grad_noalloc": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P]),
+    "tvr_phi_and_grad_f64": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
+    "tvr_phi_vjp": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P]),
+    "tvr_phi_vjp_f64": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "tvr_project_Q": (ctypes.c_int, [_P, _I64, _P]),
     "tvr_gradient_map_norm": (ctypes.c_int, [_P, _P, _P, _D, _P, _P]),
     "tvr_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),

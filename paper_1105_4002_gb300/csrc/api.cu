@@ -284,6 +284,65 @@ int tvr_phi_and_grad(const tvr_system *csys, const float *x, const float *b, dou
   return TVR_OK;
 }
 
+int tvr_phi_and_grad_f64(const tvr_system *csys, const double *x, const double *b, double alpha,
+                         double tau, double *phi_dev, double *phi_host, double *grad,
+                         double *resid, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !b || !resid) return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: null argument");
+  if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
+    return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: need alpha >= 0 and tau > 0");
+  if (!is_device_ptr(x) || !is_device_ptr(b) || !is_device_ptr(resid) ||
+      (grad && !is_device_ptr(grad)) || (phi_dev && !is_device_ptr(phi_dev)))
+    return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: vectors must be device memory");
+  if (!grad) return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: grad is required");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *pd = phi_dev ? phi_dev : sys->phi_ws;
+  const MatDev A = sys->mat();
+  launch_forward_f64(A, x, b, resid, sys->ws, s);
+  launch_backward_f64(A, resid, x, alpha, tau, grad, sys->ws, pd, s);
+  TVR_CUDA(cudaGetLastError());
+  if (phi_host) {
+    TVR_CUDA(cudaMemcpyAsync(phi_host, pd, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    TVR_CUDA(cudaStreamSynchronize(s));
+  }
+  return TVR_OK;
+}
+
+int tvr_phi_vjp(const tvr_system *csys, const float *x, const float *resid, double alpha,
+                double tau, const double *scale_dev, float *grad_x, float *grad_b, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !resid || !scale_dev || !grad_x)
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp: null argument");
+  if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp: need alpha >= 0 and tau > 0");
+  if (!is_device_ptr(x) || !is_device_ptr(resid) || !is_device_ptr(scale_dev) ||
+      !is_device_ptr(grad_x) || (grad_b && !is_device_ptr(grad_b)))
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp: vectors must be device memory");
+  prof_mark(sys, 1, 0, (cudaStream_t)stream);
+  launch_vjp(sys->mat(), resid, x, (float)alpha, (float)tau, scale_dev, grad_x, grad_b, sys->ws,
+             (cudaStream_t)stream);
+  prof_mark(sys, 1, 1, (cudaStream_t)stream);
+  TVR_CUDA(cudaGetLastError());
+  return TVR_OK;
+}
+
+int tvr_phi_vjp_f64(const tvr_system *csys, const double *x, const double *resid, double alpha,
+                    double tau, const double *scale_dev, double *grad_x, double *grad_b,
+                    void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !x || !resid || !scale_dev || !grad_x)
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp_f64: null argument");
+  if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp_f64: need alpha >= 0 and tau > 0");
+  if (!is_device_ptr(x) || !is_device_ptr(resid) || !is_device_ptr(scale_dev) ||
+      !is_device_ptr(grad_x) || (grad_b && !is_device_ptr(grad_b)))
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp_f64: vectors must be device memory");
+  launch_vjp_f64(sys->mat(), resid, x, alpha, tau, scale_dev, grad_x, grad_b, sys->ws,
+                 (cudaStream_t)stream);
+  TVR_CUDA(cudaGetLastError());
+  return TVR_OK;
+}
+
 int tvr_project_Q(float *x, int64_t n, void *stream) {
   if (n < 0 || (!x && n > 0)) return fail(TVR_ERR_ARG, "tvr_project_Q: bad arguments");
   if (n == 0) return TVR_OK;

@@ -53,7 +53,7 @@ __device__ __forceinline__ float group_sum(float v) {
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
 enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3 };
-enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3 };
+enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP = 4 };
 
 // ---------------------------------------------------------------------------
 // Forward projection.  G lanes per row, rows of a warp are consecutive (rays
@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
                const double *__restrict__ data_in, double *phi_dev, DevState *st,
-               int prof_slot = -1) {
+               int prof_slot = -1, const double *__restrict__ scale_p = nullptr,
+               float *__restrict__ gb = nullptr) {
   const float *r = rin;
   const float *x = xin;
   float *g = gout;
@@ -267,6 +268,10 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     }
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 2, G));
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 1, G));
+    if (MODE == BWD_VJP) {
+      if (valid && lane == 0) g[j] = __fmul_rn((float)*scale_p, __fmaf_rn(alpha, c, s));
+      continue;
+    }
     if (valid && lane == 0) {
       const float gj = __fmaf_rn(alpha, c, s);
       g[j] = gj;
@@ -288,6 +293,15 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     }
   }
   if (MODE == BWD_ADJ) return;
+  if (MODE == BWD_VJP) {
+    if (gb) {
+      const float sc = (float)*scale_p;
+      const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+      for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < A.m; i += stride)
+        gb[i] = -__fmul_rn(sc, r[i]);
+    }
+    return;
+  }
   FF acc[3] = {a0, a1, a2};
   double tot[3];
   if (grid_reduce<3>(acc, slot, tot) && threadIdx.x == 0) {
@@ -506,6 +520,12 @@ void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Works
                           cudaStream_t s) {
   k_backward<kColLanes, BWD_ADJ><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
       A, r, nullptr, 0.f, 1.f, 0.0, z, ws.bwd, nullptr, nullptr, nullptr);
+}
+
+void launch_vjp(const MatDev &A, const float *r, const float *x, float alpha, float tau,
+                const double *scale, float *gx, float *gb, const Workspace &ws, cudaStream_t s) {
+  k_backward<kColLanes, BWD_VJP><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, r, x, alpha, tau, (double)alpha, gx, ws.bwd, nullptr, nullptr, nullptr, -1, scale, gb);
 }
 
 void launch_tv_value(const MatDev &A, const float *x, float alpha, float tau, const Workspace &ws,

@@ -286,6 +286,16 @@ void launch_backward(const MatDev &A, const float *r, const float *x, float alph
                      float *g, const Workspace &ws, double *phi_dev, cudaStream_t s);
 void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
                           cudaStream_t s);
+void launch_vjp(const MatDev &A, const float *r, const float *x, float alpha, float tau,
+                const double *scale, float *gx, float *gb, const Workspace &ws, cudaStream_t s);
+void launch_forward_f64(const MatDev &A, const double *x, const double *b, double *r,
+                        const Workspace &ws, cudaStream_t s);
+void launch_backward_f64(const MatDev &A, const double *r, const double *x, double alpha,
+                         double tau, double *g, const Workspace &ws, double *phi_dev,
+                         cudaStream_t s);
+void launch_vjp_f64(const MatDev &A, const double *r, const double *x, double alpha, double tau,
+                    const double *scale, double *gx, double *gb, const Workspace &ws,
+                    cudaStream_t s);
 void launch_tv_value(const MatDev &A, const float *x, float alpha, float tau, const Workspace &ws,
                      double *phi_dev, cudaStream_t s);
 void launch_project(float *x, int64_t n, cudaStream_t s);
