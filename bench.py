@@ -52,6 +52,8 @@ def parse():
                     help="1: replay passes as CUDA graphs (no per-kernel timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phi-loop", type=int, default=200)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
+                    help="values of A: float32, or bfloat16 codes with per-row float32 scale")
     ap.add_argument("--pattern", default="solve", choices=["solve", "autograd"],
                     help="autograd: phi forward + backward through torch.autograd at 128^3")
     return ap.parse_args()
@@ -123,7 +125,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def captured_traffic(kernel: str):
+def captured_traffic(kernel: str, storage: str = "fp32"):
     """DRAM bytes per launch from the last ncu capture, if the kernels are unchanged since."""
     import hashlib
     try:
@@ -134,6 +136,8 @@ def captured_traffic(kernel: str):
             with open(os.path.join(ROOT, name), "rb") as f:
                 h.update(f.read())
         if h.hexdigest() != rec["kernel_sources_sha256"]:
+            return None
+        if storage != "fp32":
             return None
         return rec.get(kernel)
     except Exception:
@@ -326,7 +330,7 @@ def main():
 
     geom, x_true, z = make_problem(cfg, rank)
     t0 = time.perf_counter()
-    sysm = tvr.System(geom)
+    sysm = tvr.System(geom, storage=args.storage)
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
 
@@ -452,9 +456,12 @@ def main():
         return
 
     m, N, nnz = geom.m, geom.N, sysm.nnz
-    # algorithmic bytes per launch (solver mode; float32 values, int32 indices, int64 pointers)
-    bytes_bwd = 8 * nnz + 8 * (N + 1) + 4 * m + 3 * 4 * N     # A^T, r gather, x stencil, g, (x_prev|x+)
-    bytes_fwd = 8 * nnz + 8 * (m + 1) + 2 * 4 * N + 3 * 4 * m  # A, trial + base gathers, b, r, Ad
+    # algorithmic bytes per launch (solver mode; int32 indices, int64 pointers, values float32,
+    # or bfloat16 plus a float32 scale per row and a scaled residual)
+    vb = 4 if args.storage == "fp32" else 2
+    extra_m = 0 if args.storage == "fp32" else 8
+    bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 3 * 4 * N
+    bytes_fwd = (4 + vb) * nnz + 8 * (m + 1) + 2 * 4 * N + 3 * 4 * m + extra_m * m
     peak, peak_kind = measured_peak_gbs()
     roof = None
     if prof:
@@ -468,15 +475,15 @@ def main():
         avg_s = ms / cnt / 1e3
         ach = by / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": captured_traffic(name), "kernel": name, "launches": cnt, "avg_us": 1e6 * avg_s,
+                "traffic": captured_traffic(name, args.storage), "kernel": name, "launches": cnt, "avg_us": 1e6 * avg_s,
                 "algorithmic_bytes_per_launch": by, "peak_source": peak_kind,
                 "share_of_timed_region": ms / elapsed_ms,
                 "other": {"fwd_us": 1e3 * msf / max(nf, 1), "bwd_us": 1e3 * msb / max(nb, 1),
                           "fwd_frac": bytes_fwd / (msf / max(nf, 1) / 1e3) / 1e9 / peak if nf else None,
                           "bwd_frac": bytes_bwd / (msb / max(nb, 1) / 1e3) / 1e9 / peak if nb else None}}
     pf, pb = phi_prof["forward"], phi_prof["backward"]
-    plain_f = 8 * nnz + 8 * (m + 1) + 4 * N + 8 * m
-    plain_b = 8 * nnz + 8 * (N + 1) + 4 * m + 8 * N
+    plain_f = (4 + vb) * nnz + 8 * (m + 1) + 4 * N + 8 * m + extra_m * m
+    plain_b = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 8 * N
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
@@ -484,7 +491,7 @@ def main():
         "config": {"workload": WORKLOAD, "n": cfg.n, "views": cfg.views, "det": cfg.det,
                    "m": m, "N": N, "nnz": nnz, "alpha": cfg.alpha, "tau": cfg.tau, "eps": eps,
                    "stop": "relative gradient-map norm", "methods": ["gpbb", "upn"],
-                   "l2": L2_NOTE, "passes_as_graphs": bool(args.graph),
+                   "l2": L2_NOTE, "passes_as_graphs": bool(args.graph), "storage": args.storage,
                    "parallelism": f"{world} independent problems (one per GPU)"},
         "time_to_eps": {"gpbb_ms": sorted(t_gpbb)[len(t_gpbb) // 2],
                         "upn_ms": sorted(t_upn)[len(t_upn) // 2],

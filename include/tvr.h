@@ -56,7 +56,11 @@ typedef enum tvr_geometry_kind {
 } tvr_geometry_kind;
 
 typedef enum tvr_storage {
-  TVR_STORAGE_FP32 = 0 /* CSR and CSC, float32 values, int32 indices, int64 pointers */
+  TVR_STORAGE_FP32 = 0,         /* CSR and CSC, float32 values, int32 indices, int64 pointers */
+  TVR_STORAGE_BF16_ROWSCALE = 1 /* values a_ij = s_i q_ij: per-row FP32 scale s_i = max_j a_ij and
+                                   bfloat16 codes q_ij = bf16(a_ij / s_i) (round to nearest even),
+                                   the same codes in CSR and CSC; FP32 accumulation; the back
+                                   projection applies exactly the transpose of the forward matrix */
 } tvr_storage;
 
 /* Number of doubles per view record. */
@@ -87,7 +91,8 @@ typedef struct tvr_system tvr_system; /* opaque; owns A and all workspace */
  * grid planes are merged in increasing order (equal values once), and each
  * consecutive pair gives one entry (voxel of the midpoint, length (t_b - t_a)|d|).
  * Stores CSR (rows in traversal order) and its transpose CSC (rows ascending
- * within a column).  Synchronises `stream` once (to size the arrays).
+ * within a column), with values as `storage` says (tvr_storage).
+ * Synchronises `stream` (to size the arrays).
  * *out receives a new system owned by the caller, freed by tvr_system_free.
  * Errors: TVR_ERR_ARG (bad geometry, n^3 >= 2^31), TVR_ERR_OOM, TVR_ERR_CUDA.
  */
@@ -103,7 +108,8 @@ TVR_API int tvr_system_shape(const tvr_system *sys, int64_t *m, int64_t *N, int6
 /*
  * Copy A to caller-owned HOST buffers (synchronous): CSR row_ptr[m+1],
  * col[nnz], val[nnz]; CSC col_ptr[N+1], row[nnz], val[nnz].  Any pointer may be
- * NULL to skip that array.
+ * NULL to skip that array.  For BF16 storage val holds s_i * q_ij rounded to
+ * float32, the value the kernels apply.
  */
 TVR_API int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col, float *val);
 TVR_API int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val);

@@ -103,15 +103,18 @@ class SolveResult:
 class System:
     """A built system matrix (owns A and all device workspace)."""
 
-    def __init__(self, geometry, stream=None):
+    STORAGE = {"fp32": _capi.TVR_STORAGE_FP32, "bf16": _capi.TVR_STORAGE_BF16_ROWSCALE}
+
+    def __init__(self, geometry, stream=None, storage: str = "fp32"):
         views = np.ascontiguousarray(geometry.views, dtype=np.float64)
         self._views = views
         g = _capi.Geometry(int(geometry.n), int(views.shape[0]), int(geometry.det_cols),
                            int(geometry.det_rows), int(getattr(geometry, "kind", TVR_CONE)), 0,
                            views.ctypes.data)
         h = ctypes.c_void_p()
-        check(lib().tvr_build_system(ctypes.byref(g), _capi.TVR_STORAGE_FP32, _stream(stream),
+        check(lib().tvr_build_system(ctypes.byref(g), self.STORAGE[storage], _stream(stream),
                                      ctypes.byref(h)), "tvr_build_system")
+        self.storage = storage
         self._h = h
         m, N, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         check(lib().tvr_system_shape(h, ctypes.byref(m), ctypes.byref(N), ctypes.byref(nnz)),

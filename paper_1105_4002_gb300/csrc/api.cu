@@ -99,7 +99,8 @@ int tvr_system_free(tvr_system *sys) {
 int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_system **out) {
   if (!g || !out) return fail(TVR_ERR_ARG, "tvr_build_system: null argument");
   *out = nullptr;
-  if (storage != TVR_STORAGE_FP32) return fail(TVR_ERR_ARG, "tvr_build_system: unknown storage");
+  if (storage != TVR_STORAGE_FP32 && storage != TVR_STORAGE_BF16_ROWSCALE)
+    return fail(TVR_ERR_ARG, "tvr_build_system: unknown storage");
   if (g->n < 1 || g->n_views < 1 || g->det_cols < 1 || g->det_rows < 1 || !g->views ||
       (g->kind != TVR_CONE && g->kind != TVR_PARALLEL) || g->reserved != 0)
     return fail(TVR_ERR_ARG, "tvr_build_system: invalid geometry");
@@ -138,6 +139,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   BUILD_CUDA(cudaMalloc(&views_dev, vbytes));
   BUILD_CUDA(cudaMemcpyAsync(views_dev, g->views, vbytes, cudaMemcpyHostToDevice, s));
   BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
+  if (storage == TVR_STORAGE_BF16_ROWSCALE) BUILD_CUDA(quantize_bf16(sys->A, s));
   sys->nnz = sys->A.nnz;
   // reduction workspace: per slot partials + counter + outputs
   const size_t part = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;
@@ -174,16 +176,42 @@ int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col,
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
-  return export_compact(sys->A.row_ptr, sys->A.row_len, sys->A.col, sys->A.val, sys->m,
-                        sys->A.nnz_pad, row_ptr, col, val);
+  const float *vd = sys->A.val;
+  float *tmp = nullptr;
+  if (val && sys->A.storage == TVR_STORAGE_BF16_ROWSCALE) {
+    TVR_CUDA(cudaMalloc(&tmp, sizeof(float) * (sys->A.nnz_pad > 0 ? sys->A.nnz_pad : 1)));
+    cudaError_t e = effective_values(sys->A, false, tmp, 0);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(e, "effective_values");
+    }
+    vd = tmp;
+  }
+  int rc = export_compact(sys->A.row_ptr, sys->A.row_len, sys->A.col, vd, sys->m, sys->A.nnz_pad,
+                          row_ptr, col, val);
+  if (tmp) cudaFree(tmp);
+  return rc;
 }
 
 int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val) {
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
-  return export_compact(sys->A.col_ptr, sys->A.col_len, sys->A.row, sys->A.cval, sys->N,
-                        sys->A.nnz_cpad, col_ptr, row, val);
+  const float *vd = sys->A.cval;
+  float *tmp = nullptr;
+  if (val && sys->A.storage == TVR_STORAGE_BF16_ROWSCALE) {
+    TVR_CUDA(cudaMalloc(&tmp, sizeof(float) * (sys->A.nnz_cpad > 0 ? sys->A.nnz_cpad : 1)));
+    cudaError_t e = effective_values(sys->A, true, tmp, 0);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(e, "effective_values");
+    }
+    vd = tmp;
+  }
+  int rc = export_compact(sys->A.col_ptr, sys->A.col_len, sys->A.row, vd, sys->N, sys->A.nnz_cpad,
+                          col_ptr, row, val);
+  if (tmp) cudaFree(tmp);
+  return rc;
 }
 
 int tvr_forward(const tvr_system *csys, const float *x, float *y, void *stream) {
@@ -254,8 +282,13 @@ int tvr_phi_and_grad(const tvr_system *csys, const float *x, const float *b, dou
   }
   double *pd = phi_dev ? phi_dev : sys->phi_ws;
   const MatDev A = sys->mat();
+  float *rsd = nullptr;  // BF16 storage: the back projection gathers s_i r_i
+  if (A.bf16 && grad) {
+    if ((rc = ensure_vec(&sys->stage_rsM, sys->m))) return rc;
+    rsd = sys->stage_rsM;
+  }
   prof_mark(sys, 0, 0, s);
-  launch_forward(A, xd, bd, rd, sys->ws, s);
+  launch_forward(A, xd, bd, rd, sys->ws, s, rsd);
   prof_mark(sys, 0, 1, s);
   if (grad) {
     const bool gh = !is_device_ptr(grad);
@@ -265,7 +298,7 @@ int tvr_phi_and_grad(const tvr_system *csys, const float *x, const float *b, dou
       gd = sys->stage_gN;
     }
     prof_mark(sys, 1, 0, s);
-    launch_backward(A, rd, xd, (float)alpha, (float)tau, gd, sys->ws, pd, s);
+    launch_backward(A, rsd ? rsd : rd, xd, (float)alpha, (float)tau, gd, sys->ws, pd, s);
     prof_mark(sys, 1, 1, s);
     if (gh) {
       TVR_CUDA(cudaMemcpyAsync(grad, gd, sizeof(float) * sys->N, cudaMemcpyDeviceToHost, s));
@@ -295,6 +328,8 @@ int tvr_phi_and_grad_f64(const tvr_system *csys, const double *x, const double *
       (grad && !is_device_ptr(grad)) || (phi_dev && !is_device_ptr(phi_dev)))
     return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: vectors must be device memory");
   if (!grad) return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: grad is required");
+  if (sys->A.storage != TVR_STORAGE_FP32)
+    return fail(TVR_ERR_ARG, "tvr_phi_and_grad_f64: needs a system with FP32 storage");
   cudaStream_t s = (cudaStream_t)stream;
   double *pd = phi_dev ? phi_dev : sys->phi_ws;
   const MatDev A = sys->mat();
@@ -337,6 +372,8 @@ int tvr_phi_vjp_f64(const tvr_system *csys, const double *x, const double *resid
   if (!is_device_ptr(x) || !is_device_ptr(resid) || !is_device_ptr(scale_dev) ||
       !is_device_ptr(grad_x) || (grad_b && !is_device_ptr(grad_b)))
     return fail(TVR_ERR_ARG, "tvr_phi_vjp_f64: vectors must be device memory");
+  if (sys->A.storage != TVR_STORAGE_FP32)
+    return fail(TVR_ERR_ARG, "tvr_phi_vjp_f64: needs a system with FP32 storage");
   launch_vjp_f64(sys->mat(), resid, x, alpha, tau, scale_dev, grad_x, grad_b, sys->ws,
                  (cudaStream_t)stream);
   TVR_CUDA(cudaGetLastError());

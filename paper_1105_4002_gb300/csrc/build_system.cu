@@ -460,7 +460,8 @@ cudaError_t transpose(MatStore &A, cudaStream_t s) {
 }  // namespace
 
 void free_matrix(MatStore &A) {
-  void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col, A.row, A.val, A.cval};
+  void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col,   A.row,
+                  A.val,     A.cval,    A.qval,    A.qcval,   A.rscale};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   A = MatStore{};
@@ -512,4 +513,76 @@ cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kin
   if (A.nnz_pad == 0) return cudaStreamSynchronize(s);
   if (A.nnz_pad >= ((int64_t)1 << 31)) return transpose<int64_t>(A, s);
   return transpose<int32_t>(A, s);
+}
+
+// ---- BF16 storage with per-row scale ----
+namespace {
+
+__global__ void k_row_scale(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ row_len,
+                            const float *__restrict__ val, int64_t m, float *__restrict__ sc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  float mx = 0.f;
+  for (int k = 0; k < row_len[i]; ++k) mx = fmaxf(mx, val[row_ptr[i] + k]);
+  sc[i] = mx > 0.f ? mx : 1.f;
+}
+
+// q = bf16_rn(a / s_row) for real entries, 0 for padding.  Thread per row (CSR)
+// or per column (CSC, row of each entry from `rows`).
+__global__ void k_quantize(const int64_t *__restrict__ ptr, const int32_t *__restrict__ len,
+                           const int32_t *__restrict__ rows, const float *__restrict__ val,
+                           const float *__restrict__ sc, int64_t nseg,
+                           __nv_bfloat16 *__restrict__ q) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nseg) return;
+  const int64_t o = ptr[c], end = ptr[c + 1];
+  for (int64_t e = o; e < end; ++e) {
+    if (e - o < len[c]) {
+      const float s = sc[rows ? rows[e] : c];
+      q[e] = __float2bfloat16_rn(__fdiv_rn(val[e], s));
+    } else {
+      q[e] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+__global__ void k_effective(const int64_t *__restrict__ ptr, const int32_t *__restrict__ rows,
+                            const __nv_bfloat16 *__restrict__ q, const float *__restrict__ sc,
+                            int64_t nseg, float *__restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nseg) return;
+  for (int64_t e = ptr[c]; e < ptr[c + 1]; ++e)
+    out[e] = __fmul_rn(sc[rows ? rows[e] : c], __bfloat162float(q[e]));
+}
+
+}  // namespace
+
+// Replace the FP32 values by per-row scales and BF16 codes (CSR and CSC get
+// the same code for the same entry: the same quotient, rounded once).
+cudaError_t quantize_bf16(MatStore &A, cudaStream_t s) {
+  BM_TRY(owned(&A.rscale, A.m));
+  BM_TRY(owned(&A.qval, A.nnz_pad));
+  BM_TRY(owned(&A.qcval, A.nnz_cpad));
+  k_row_scale<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, A.val, A.m, A.rscale);
+  k_quantize<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, nullptr, A.val, A.rscale,
+                                                   A.m, A.qval);
+  k_quantize<<<blocks_for(A.N), TVR_BLOCK, 0, s>>>(A.col_ptr, A.col_len, A.row, A.cval, A.rscale,
+                                                   A.N, A.qcval);
+  BM_TRY(cudaGetLastError());
+  BM_TRY(cudaStreamSynchronize(s));
+  cudaFree(A.val);
+  cudaFree(A.cval);
+  A.val = A.cval = nullptr;
+  A.storage = TVR_STORAGE_BF16_ROWSCALE;
+  return cudaSuccess;
+}
+
+// FP32 values the kernels apply, in stored (padded) order: CSR or CSC.
+cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s) {
+  if (csc)
+    k_effective<<<blocks_for(A.N), TVR_BLOCK, 0, s>>>(A.col_ptr, A.row, A.qcval, A.rscale, A.N, out);
+  else
+    k_effective<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, nullptr, A.qval, A.rscale, A.m, out);
+  BM_TRY(cudaGetLastError());
+  return cudaStreamSynchronize(s);
 }

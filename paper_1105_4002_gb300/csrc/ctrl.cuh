@@ -175,6 +175,7 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
     if (st->k == 0) st->gnorm0 = st->gnorm;
     st_swap(st->vN[RN_X], st->vN[RN_T]);
     st_swap(st->vM[RM_R], st->vM[RM_RT]);
+    st_swap(st->vM[RM_RS], st->vM[RM_RTS]);
     const int tr = st->trial;
     st->trial = 0;
     st->need_grad = 1;
@@ -221,6 +222,7 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
   }
   st_swap(st->vN[RN_X], st->vN[RN_T]);
   st_swap(st->vM[RM_R], st->vM[RM_RT]);
+  st_swap(st->vM[RM_RS], st->vM[RM_RTS]);
   const int tr = st->trial;
   st->trial = 0;
   st->need_grad = 1;

@@ -52,6 +52,19 @@ __device__ __forceinline__ float group_sum(float v) {
 
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
+// Four stored values at a 4-aligned position: float32, or bfloat16 codes
+// widened to float32 (a bfloat16 is the upper half of a float32's bits).
+template <bool BF>
+__device__ __forceinline__ float4 load4(const float *__restrict__ v32,
+                                        const __nv_bfloat16 *__restrict__ v16, int64_t e) {
+  if (BF) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(v16 + e));
+    return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                       __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+  }
+  return __ldg(reinterpret_cast<const float4 *>(v32 + e));
+}
+
 enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3 };
 enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP = 4 };
 
@@ -59,19 +72,22 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // Forward projection.  G lanes per row, rows of a warp are consecutive (rays
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
-template <int G, int MODE>
+template <int G, int MODE, bool BF>
 __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
-              float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1) {
+              float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1,
+              float *__restrict__ rsout = nullptr) {
   const float *x = xin;
   const float2 *xd = nullptr;  // trial mode: (xbar, xbar - base) per voxel
   float *r = rout;
+  float *rs = rsout;           // BF16 storage: r times the row scale
   float *ad = nullptr;
   if (MODE == FWD_INIT) {
     const bool upn = st->solver == SOLVER_UPN;
     b = st->b;
     x = upn ? st->vN[RN_Y] : st->vN[RN_X];
     r = upn ? st->vM[RM_RY] : st->vM[RM_R];
+    rs = upn ? st->vM[RM_RYS] : st->vM[RM_RS];
   } else if (MODE == FWD_TRIAL) {
     if (st->done) return;
     if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->prof_flags[prof_slot] = 1;
@@ -79,6 +95,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     b = st->b;
     xd = st->t2;
     r = st->vM[RM_RT];
+    rs = st->vM[RM_RTS];
     ad = upn ? st->vM[RM_AD] : nullptr;
   }
   constexpr int RPW = 32 / G;
@@ -108,7 +125,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
         const int64_t e = e0 + (int64_t)u * 4 * G;
         if (e < end) {
           c4[u] = __ldg(reinterpret_cast<const int4 *>(A.col + e));
-          v4[u] = __ldg(reinterpret_cast<const float4 *>(A.val + e));
+          v4[u] = load4<BF>(A.val, A.qval, e);
         } else {
           c4[u] = make_int4(0, 0, 0, 0);
           v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -141,11 +158,18 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     sx = group_sum<G>(sx);
     if (MODE == FWD_TRIAL) sd = group_sum<G>(sd);
     if (valid && lane == 0) {
+      float sc = 1.f;
+      if (BF) {
+        sc = __ldg(A.rscale + row);
+        sx = __fmul_rn(sc, sx);
+        sd = __fmul_rn(sc, sd);
+      }
       if (MODE == FWD_Y) {
         r[row] = sx;
       } else {
         const float ri = __fsub_rn(sx, __ldg(b + row));
         r[row] = ri;
+        if (BF && rs) rs[row] = __fmul_rn(sc, ri);
         ff_add_prod(a0, ri, ri);
         if (MODE == FWD_TRIAL) {
           if (ad) ad[row] = sd;
@@ -172,7 +196,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
 // lanes 0..3 of a group evaluate the Huber weights of voxels j, j-ex, j-ey,
 // j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
 // ---------------------------------------------------------------------------
-template <int G, int MODE>
+template <int G, int MODE, bool BF>
 __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
@@ -195,12 +219,12 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     tau = (float)st->tau;
     if (kind == SOLVER_UPN) {
       x = st->vN[RN_Y];
-      r = st->vM[RM_RY];
+      r = BF ? st->vM[RM_RYS] : st->vM[RM_RY];
       g = st->vN[RN_G];
       if (MODE == BWD_SOLVER) q = st->vN[RN_X];
     } else {
       x = st->vN[RN_X];
-      r = st->vM[RM_R];
+      r = BF ? st->vM[RM_RS] : st->vM[RM_R];
       g = st->vN[RN_G];
       if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
         g = st->vN[RN_GN];
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
         const int64_t e = e0 + (int64_t)u * 4 * G;
         if (e < end) {
           i4[u] = __ldg(reinterpret_cast<const int4 *>(A.row + e));
-          v4[u] = __ldg(reinterpret_cast<const float4 *>(A.cval + e));
+          v4[u] = load4<BF>(A.cval, A.qcval, e);
         } else {
           i4[u] = make_int4(0, 0, 0, 0);
           v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -243,8 +267,14 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
 #pragma unroll
       for (int u = 0; u < kColChunks; ++u) {
         if (e0 + (int64_t)u * 4 * G >= end) break;
-        const float r0 = __ldg(r + i4[u].x), r1 = __ldg(r + i4[u].y);
-        const float r2 = __ldg(r + i4[u].z), r3 = __ldg(r + i4[u].w);
+        float r0 = __ldg(r + i4[u].x), r1 = __ldg(r + i4[u].y);
+        float r2 = __ldg(r + i4[u].z), r3 = __ldg(r + i4[u].w);
+        if (BF && (MODE == BWD_ADJ || MODE == BWD_VJP)) {  // caller's r: apply the row scales
+          r0 = __fmul_rn(r0, __ldg(A.rscale + i4[u].x));
+          r1 = __fmul_rn(r1, __ldg(A.rscale + i4[u].y));
+          r2 = __fmul_rn(r2, __ldg(A.rscale + i4[u].z));
+          r3 = __fmul_rn(r3, __ldg(A.rscale + i4[u].w));
+        }
         s = __fmaf_rn(v4[u].x, r0, s);
         s = __fmaf_rn(v4[u].y, r1, s);
         s = __fmaf_rn(v4[u].z, r2, s);
@@ -413,7 +443,9 @@ __global__ void __launch_bounds__(TVR_BLOCK) k_yform(MatDev A, RedSlot slot, Dev
     if (i < A.m) {
       const float u = __fmaf_rn(bp, U[i], AD[i]);
       U[i] = u;
-      RY[i] = __fmaf_rn(beta, u, R[i]);
+      const float ry = __fmaf_rn(beta, u, R[i]);
+      RY[i] = ry;
+      if (A.bf16) st->vM[RM_RYS][i] = __fmul_rn(A.rscale[i], ry);
       ff_add_prod(a1, u, u);
     }
   }
@@ -495,36 +527,50 @@ int occupancy_grid(const void *kernel, int block, int device) {
 }
 
 void kernel_grids(Workspace &ws, int device) {
-  ws.grid_fwd = occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL>, TVR_BLOCK, device);
-  ws.grid_bwd = occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER>, TVR_BLOCK, device);
+  ws.grid_fwd =
+      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device);
+  ws.grid_bwd =
+      occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device);
   ws.grid_elem = occupancy_grid((const void *)k_step, TVR_BLOCK, device);
 }
 
+// Kernel instance for the system's storage (float32 or bfloat16 values).
+template <int MODE>
+auto fwd_kernel(const MatDev &A) {
+  return A.bf16 ? k_forward<kRowLanes, MODE, true> : k_forward<kRowLanes, MODE, false>;
+}
+template <int MODE>
+auto bwd_kernel(const MatDev &A) {
+  return A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>;
+}
+
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
-                    cudaStream_t s) {
-  k_forward<kRowLanes, FWD_RESID><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, b, r, ws.fwd, nullptr);
+                    cudaStream_t s, float *rs) {
+  fwd_kernel<FWD_RESID>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, b, r, ws.fwd, nullptr, -1, rs);
 }
 
 void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
                           cudaStream_t s) {
-  k_forward<kRowLanes, FWD_Y><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, nullptr, y, ws.fwd, nullptr);
+  fwd_kernel<FWD_Y>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, nullptr, y, ws.fwd, nullptr, -1,
+                                                          nullptr);
 }
 
 void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                      float *g, const Workspace &ws, double *phi_dev, cudaStream_t s) {
-  k_backward<kColLanes, BWD_GRAD><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, r, x, alpha, tau, (double)alpha, g, ws.bwd, ws.fwd.out, phi_dev, nullptr);
+  bwd_kernel<BWD_GRAD>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, r, x, alpha, tau, (double)alpha, g, ws.bwd, ws.fwd.out, phi_dev, nullptr, -1, nullptr,
+      nullptr);
 }
 
 void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
                           cudaStream_t s) {
-  k_backward<kColLanes, BWD_ADJ><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, r, nullptr, 0.f, 1.f, 0.0, z, ws.bwd, nullptr, nullptr, nullptr);
+  bwd_kernel<BWD_ADJ>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, r, nullptr, 0.f, 1.f, 0.0, z, ws.bwd, nullptr, nullptr, nullptr, -1, nullptr, nullptr);
 }
 
 void launch_vjp(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                 const double *scale, float *gx, float *gb, const Workspace &ws, cudaStream_t s) {
-  k_backward<kColLanes, BWD_VJP><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+  bwd_kernel<BWD_VJP>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
       A, r, x, alpha, tau, (double)alpha, gx, ws.bwd, nullptr, nullptr, nullptr, -1, scale, gb);
 }
 
@@ -544,10 +590,11 @@ void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, cons
 }
 
 void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
-  k_forward<kRowLanes, FWD_INIT><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr,
-                                                                   ws.fwd, st);
-  k_backward<kColLanes, BWD_INIT><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st);
+  fwd_kernel<FWD_INIT>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr, ws.fwd,
+                                                             st, -1, nullptr);
+  bwd_kernel<BWD_INIT>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st, -1, nullptr,
+      nullptr);
 }
 
 // One pass: [UPN: extrapolation] -> gradient at the new point (skipped after a
@@ -557,14 +604,13 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
   if (solver == SOLVER_UPN)
     k_yform<<<elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.yf, st);
   if (tm) cudaEventRecord(tm->ev[1][0], s);
-  k_backward<kColLanes, BWD_SOLVER><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
+  bwd_kernel<BWD_SOLVER>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
       A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st,
-      tm ? tm->slot[1] : -1);
+      tm ? tm->slot[1] : -1, nullptr, nullptr);
   if (tm) cudaEventRecord(tm->ev[1][1], s);
   k_step<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.step, st);
   if (tm) cudaEventRecord(tm->ev[0][0], s);
-  k_forward<kRowLanes, FWD_TRIAL><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr,
-                                                                    ws.fwd, st,
-                                                                    tm ? tm->slot[0] : -1);
+  fwd_kernel<FWD_TRIAL>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(
+      A, nullptr, nullptr, nullptr, ws.fwd, st, tm ? tm->slot[0] : -1, nullptr);
   if (tm) cudaEventRecord(tm->ev[0][1], s);
 }

@@ -59,6 +59,8 @@ extern "C" int tvr_phi_and_grad_noalloc(const tvr_system *sys, const float *x, c
   if (!sys || !x || !b) return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: null argument");
   if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
     return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: need alpha >= 0 and tau > 0");
+  if (sys->A.storage != TVR_STORAGE_FP32)
+    return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: needs a system with FP32 storage");
   if (sys->m > kNoallocMaxRows)
     return tvr_fail(TVR_ERR_ARG,
                     "tvr_phi_and_grad_noalloc: the system has more rays than the static scratch "

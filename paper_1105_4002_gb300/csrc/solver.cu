@@ -22,8 +22,9 @@ namespace {
 int ensure_solver(tvr_system *sys, int64_t hist_records) {
   for (auto &p : sys->vN)
     if (int rc = ensure_vec(&p, sys->N)) return rc;
-  for (auto &p : sys->vM)
-    if (int rc = ensure_vec(&p, sys->m)) return rc;
+  const int nm = sys->A.storage == TVR_STORAGE_BF16_ROWSCALE ? RM_COUNT : RM_RS;
+  for (int k = 0; k < nm; ++k)
+    if (int rc = ensure_vec(&sys->vM[k], sys->m)) return rc;
   if (!sys->t2) TVR_CUDA(cudaMalloc(&sys->t2, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));
   if (!sys->st) TVR_CUDA(cudaMalloc(&sys->st, sizeof(DevState)));
   if (!sys->pinned_flag) TVR_CUDA(cudaMallocHost(&sys->pinned_flag, 64));

@@ -28,6 +28,7 @@ struct tvr_system {
   Workspace ws{};
   // staging and scratch vectors (allocated on first use)
   float *stage_xN = nullptr, *stage_gN = nullptr, *stage_bM = nullptr, *stage_rM = nullptr;
+  float *stage_rsM = nullptr;  // BF16 storage: scaled residual for the back projection
   double *phi_ws = nullptr;  // 4 doubles
   // solver workspace (allocated on first solve)
   DevState *st = nullptr;
@@ -63,6 +64,10 @@ struct tvr_system {
     d.col_ptr = A.col_ptr;
     d.row = A.row;
     d.cval = A.cval;
+    d.bf16 = A.storage == TVR_STORAGE_BF16_ROWSCALE;
+    d.qval = A.qval;
+    d.qcval = A.qcval;
+    d.rscale = A.rscale;
     return d;
   }
 };

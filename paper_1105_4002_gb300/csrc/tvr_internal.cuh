@@ -1,6 +1,7 @@
 // Internal declarations of libtvr: device helpers, solver state, launchers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -224,7 +225,10 @@ __device__ __forceinline__ float huber_bregman(const float z[3], float nz, const
 enum SolverKind { SOLVER_NONE = 0, SOLVER_GP = 1, SOLVER_GPBB = 2, SOLVER_UPN = 3 };
 
 enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_COUNT };
-enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_COUNT };
+// RS, RTS, RYS: the residuals R, RT, RY times the per-row scales (BF16 storage
+// only), which the back projection gathers so that it applies the same
+// matrix s_i q_ij as the forward projection.
+enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_RS, RM_RTS, RM_RYS, RM_COUNT };
 
 #define TVR_FHIST 16
 
@@ -269,6 +273,11 @@ struct MatDev {
   const int64_t *col_ptr;  // CSC [N+1], every column padded to a multiple of 4 entries
   const int32_t *row;      // [stored]
   const float *cval;       // [stored]
+  // BF16 storage: a_ij = rscale[i] * q_ij, the same codes q in CSR and CSC
+  int bf16;
+  const __nv_bfloat16 *qval;   // CSR codes [stored]
+  const __nv_bfloat16 *qcval;  // CSC codes [stored]
+  const float *rscale;         // [m]
 };
 
 struct Workspace {
@@ -279,7 +288,7 @@ struct Workspace {
 // Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from
 // the device state); st == nullptr is the plain mode with explicit pointers.
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
-                    cudaStream_t s);
+                    cudaStream_t s, float *rs = nullptr);
 void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
                           cudaStream_t s);
 void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
@@ -326,13 +335,18 @@ struct MatStore {
   int64_t *row_ptr = nullptr, *col_ptr = nullptr;  // padded offsets [m+1], [N+1]
   int32_t *row_len = nullptr, *col_len = nullptr;  // real counts [m], [N]
   int32_t *col = nullptr, *row = nullptr;
-  float *val = nullptr, *cval = nullptr;
+  float *val = nullptr, *cval = nullptr;  // FP32 storage (null for BF16)
+  int storage = TVR_STORAGE_FP32;
+  __nv_bfloat16 *qval = nullptr, *qcval = nullptr;  // BF16 codes (null for FP32)
+  float *rscale = nullptr;                          // BF16 per-row scales [m]
 };
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
                                cudaStream_t s);
 int64_t scan_tmp_len(int64_t n);
 cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
                          int64_t N, MatStore &A, cudaStream_t s);
+cudaError_t quantize_bf16(MatStore &A, cudaStream_t s);
+cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s);
 void free_matrix(MatStore &A);
 
 int occupancy_grid(const void *kernel, int block, int device);
