@@ -272,6 +272,25 @@ TVR_API int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, d
                   const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream);
 
 /*
+ * Parameter sweep: k <= 8 solves of the same system and data b with
+ * regularisation parameters alphas[0..k-1] (same tau, eps and options), run in
+ * lockstep so that every forward and back projection reads A once for all of
+ * them (sparse matrix times 8 interleaved vectors).  method: 1 = GP, 2 = GPBB,
+ * 3 = UPN, each exactly as in tvr_solve_gp / _gpbb / _upn, per column.
+ * X holds k columns of N floats (column c at X + c*N, host or device):
+ * x^(0) on entry, x* on return.  infos: nullable HOST array of k records
+ * (phi is not evaluated: NaN).  Each column stops on its own test; a stopped
+ * column is masked out of the later passes.  Synchronises `stream`.
+ * Returns TVR_OK if every column converged, else the first error status of a
+ * column, else TVR_NOT_CONVERGED.  Not an entry of the paper: a batching of
+ * its methods over alpha.
+ */
+TVR_API int tvr_solve_sweep(const tvr_system *sys, int32_t method, const float *b,
+                            const double *alphas, int32_t k, double tau, double eps,
+                            const tvr_solve_opts *opts, float *X, tvr_solve_info *infos,
+                            void *stream);
+
+/*
  * Kernel timing for measurement: while enabled, the library records a CUDA
  * event pair on the launch stream around every forward (CSR) and back (CSC +
  * TV) projection kernel launched outside a CUDA graph.  tvr_profile_read

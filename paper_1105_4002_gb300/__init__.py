@@ -229,6 +229,35 @@ class System:
                            stop_value=info.stop_value, L=info.L, theta=info.theta, mu=info.mu,
                            history=hist[:info.history_used].copy() if hist is not None else None)
 
+    def solve_sweep(self, method: str, b, alphas, tau: float, eps: float, X,
+                    opts: SolveOptions | None = None, stream=None):
+        """Solve for up to 8 alphas at once (columns of X: x0 in, x* out); list of results."""
+        code = {"gp": 1, "gpbb": 2, "upn": 3}[method]
+        k = len(alphas)
+        al = (ctypes.c_double * k)(*[float(a) for a in alphas])
+        co = self._opts(opts)
+        pb, _ = _ptr(b, self.m, "b")
+        px, _ = _ptr(X, k * self.N, "X")
+        infos = (_capi.SolveInfo * k)()
+        st = lib().tvr_solve_sweep(self._h, code, pb, ctypes.cast(al, ctypes.c_void_p), k,
+                                   float(tau), float(eps), ctypes.byref(co), px, infos,
+                                   _stream(stream, b, X))
+        check(st, "tvr_solve_sweep", allow=(TVR_OK, TVR_NOT_CONVERGED))
+        return [SolveResult(status=i.status, iters=i.iters, f_evals=i.f_evals, g_evals=i.g_evals,
+                            trials=i.trials, passes=i.passes, phi=i.phi, gnorm=i.gnorm,
+                            gnorm0=i.gnorm0, stop_value=i.stop_value, L=i.L, theta=i.theta,
+                            mu=i.mu) for i in infos]
+
+    def _opts(self, opts):
+        o = opts or SolveOptions()
+        co = _capi.SolveOpts()
+        lib().tvr_solve_opts_default(ctypes.byref(co))
+        for f in ("k_max", "stop_mode", "gpbb_K", "gpbb_max_trials", "bt_max", "batch",
+                  "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
+            setattr(co, f, getattr(o, f))
+        co.use_graph = 1 if o.use_graph else 0
+        return co
+
     # ---- measurement ----
     def profile(self, enable: bool):
         check(lib().tvr_profile_enable(self._h, 1 if enable else 0), "tvr_profile_enable")

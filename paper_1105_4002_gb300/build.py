@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtvr.so")
 
-SOURCES = ["kernels.cu", "kernels_f64.cu", "build_system.cu", "api.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "kernels_f64.cu", "build_system.cu", "api.cu", "solver.cu", "sweep.cu", "noalloc.cu"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",

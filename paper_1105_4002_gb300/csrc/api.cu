@@ -82,6 +82,8 @@ int tvr_system_free(tvr_system *sys) {
       for (int w = 0; w < 2; ++w)
         if (sys->prof_ev[k][i][w]) cudaEventDestroy(sys->prof_ev[k][i][w]);
   free_matrix(sys->A);
+  sweep_free(sys->sweep);
+  if (sys->stage_sweepX) cudaFree(sys->stage_sweepX);
   void *ptrs[] = {sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
                   sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev, sys->t2};
   for (void *p : ptrs)

@@ -17,6 +17,9 @@ int tvr_cuda_fail(cudaError_t e, const char *what);
   } while (0)
 
 constexpr int kSlots = 6;
+
+struct tvr_sweep_mem;  // device memory of parameter sweeps (sweep.cu)
+void sweep_free(tvr_sweep_mem *m);
 constexpr int kProfPairs = TVR_PROF_PAIRS;
 
 struct tvr_system {
@@ -29,6 +32,8 @@ struct tvr_system {
   // staging and scratch vectors (allocated on first use)
   float *stage_xN = nullptr, *stage_gN = nullptr, *stage_bM = nullptr, *stage_rM = nullptr;
   float *stage_rsM = nullptr;  // BF16 storage: scaled residual for the back projection
+  float *stage_sweepX = nullptr;  // host x0 / x* of a sweep, 8 columns
+  tvr_sweep_mem *sweep = nullptr;
   double *phi_ws = nullptr;  // 4 doubles
   // solver workspace (allocated on first solve)
   DevState *st = nullptr;

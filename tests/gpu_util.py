@@ -38,3 +38,17 @@ def geometries():
     dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, 1, 1], [0.3, -0.7, 0.2]])
     out.append(("parallel_axes_diag", synth.parallel_geometry(6, dirs, 9)))
     return out
+
+
+def oracle_spread(prob, solver, eps, draws=4, seed=0):
+    """How far the oracle's own answer moves when b is perturbed at the
+    relative size of float32 gradient error (1e-6): the largest relative L2
+    distance over `draws` seeded perturbations, and the solution itself."""
+    ref = solver(prob, np.zeros(prob.N), eps)
+    rng = np.random.default_rng(seed)
+    spread = 0.0
+    for _ in range(draws):
+        pb = prob.b * (1 + 1e-6 * rng.standard_normal(prob.b.size))
+        p2 = oracle.Problem(A=prob.A, b=pb, n=prob.n, alpha=prob.alpha, tau=prob.tau)
+        spread = max(spread, rel_l2(solver(p2, np.zeros(prob.N), eps).x, ref.x))
+    return ref, spread
