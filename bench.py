@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--phi-loop", type=int, default=200)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
                     help="values of A: float32, or bfloat16 codes with per-row float32 scale")
-    ap.add_argument("--pattern", default="solve", choices=["solve", "autograd"],
+    ap.add_argument("--pattern", default="solve", choices=["solve", "autograd", "batch"],
                     help="autograd: phi forward + backward through torch.autograd at 128^3")
     return ap.parse_args()
 
@@ -292,6 +292,110 @@ def run_autograd(args):
         "clocks": clocks}), flush=True)
 
 
+# ------------------------------------------------------------- batching
+def batch_problems(count=48, seed=5):
+    """Uneven problems: edge U{24..96}, views U{8..40}, detector 1.5 x edge (seeded)."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(24, 97))
+        v = int(rng.integers(8, 41))
+        p = int(round(1.5 * n))
+        g = synth.cone_geometry(n, v, p, 3.0 * n, 2.0 * n)
+        x_true = synth.ellipsoid_phantom(n, 10, (n / 16, n / 3.2), (0.0, 1.0), 5000 + i)
+        z = synth.standard_normal(g.m, 6000 + i)
+        out.append((g, x_true, z))
+    return out
+
+
+def run_batch(args):
+    """solves/s to eps: 48 uneven problems batched vs one by one; 8-alpha sweep at 128^3."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    dev = torch.device("cuda", 0)
+    eps, alpha, tau = 1e-4, 1e-2, 1e-4
+    res = {}
+
+    def make_b(sysm, x_true, z, level):
+        xt = torch.tensor(x_true, dtype=torch.float32, device=dev)
+        ax = torch.empty(sysm.m, dtype=torch.float32, device=dev)
+        sysm.forward(xt, ax)
+        axh = ax.cpu().numpy().astype(np.float64)
+        return torch.tensor((axh + level * np.linalg.norm(axh) / math.sqrt(sysm.m) * z)
+                            .astype(np.float32), device=dev)
+
+    probs = batch_problems()
+    for storage in ("fp32", "bf16"):
+        systems = [tvr.System(g, storage=storage) for g, _, _ in probs]
+        bs = [make_b(s_, xt, z, 0.01) for s_, (g, xt, z) in zip(systems, probs)]
+        xs = [torch.zeros(s_.N, device=dev) for s_ in systems]
+        al = [alpha] * len(systems)
+        tvr.solve_batch("upn", systems, bs, al, tau, eps, xs)          # warm-up (graphs, buffers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for x in xs:
+                x.zero_()
+            rb = tvr.solve_batch("upn", systems, bs, al, tau, eps, xs)
+        torch.cuda.synchronize()
+        t_batch = (time.perf_counter() - t0) / args.steps
+        t0 = time.perf_counter()
+        for s_, b, x in zip(systems, bs, xs):
+            s_.solve("upn", b, alpha, tau, eps, x.zero_())
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        res[f"batch48_{storage}"] = {
+            "solves_per_s": len(systems) / t_batch, "ms": 1e3 * t_batch,
+            "one_by_one_solves_per_s": len(systems) / t_seq,
+            "converged": sum(r.status == 0 for r in rb), "iters_total": sum(r.iters for r in rb)}
+        del systems, bs, xs
+        torch.cuda.empty_cache()
+
+    cfg = synth.get_config("c128")
+    alphas = list(np.logspace(-4, -1, 8))
+    for storage in ("fp32", "bf16"):
+        sysm = tvr.System(cfg.geometry(), storage=storage)
+        b = make_b(sysm, cfg.phantom(), synth.standard_normal(sysm.m, cfg.seed + 1000), cfg.noise)
+        X = torch.zeros(8 * sysm.N, device=dev)
+        sysm.solve_sweep("upn", b, alphas, tau, eps, X)                # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = sysm.solve_sweep("upn", b, alphas, tau, eps, X.zero_())
+        torch.cuda.synchronize()
+        t_sw = time.perf_counter() - t0
+        x1 = torch.zeros(sysm.N, device=dev)
+        sysm.solve("upn", b, alphas[0], tau, eps, x1)                    # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = []
+        for a in alphas:
+            its.append(sysm.solve("upn", b, a, tau, eps, x1.zero_()).iters)
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t0
+        res[f"sweep8_128cubed_{storage}"] = {
+            "solves_per_s": 8 / t_sw, "ms": 1e3 * t_sw, "single_solves_per_s": 8 / t_single,
+            "converged": sum(r.status == 0 for r in rs), "iters": [r.iters for r in rs],
+            "single_iters": its}
+        del sysm, X
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "solves/s to eps=1e-4 (UPN): 48 uneven problems batched; 8-alpha sweep at 128^3",
+        "value": res["batch48_fp32"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "48 problems: edge U{24..96}, views U{8..40}, detector 1.5 edge, "
+                               "10 ellipsoids, 1% noise; sweep: 128^3 / 60 views / 192^2, "
+                               "alphas 1e-4..1e-1 log-spaced", "alpha": alpha, "tau": tau,
+                   "eps": eps},
+        "results": res}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -309,6 +413,10 @@ def main():
     if args.pattern == "autograd":
         if rank == 0:
             run_autograd(args)
+        return
+    if args.pattern == "batch":
+        if rank == 0:
+            run_batch(args)
         return
 
     import numpy as np

@@ -272,6 +272,23 @@ TVR_API int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, d
                   const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream);
 
 /*
+ * Batch of independent problems (each its own system, data b, alpha and
+ * x^(0) / x*): solves them with one method (1 = GP, 2 = GPBB, 3 = UPN) at the
+ * same tau, eps and options, interleaved on one stream per system so that
+ * small problems run concurrently on the GPU.  Arrays of `count` pointers
+ * (HOST arrays; the vectors they point to are host or device, as in the
+ * single solves); a system may appear only once.  infos: nullable HOST array
+ * of count records.  Synchronises `stream` at entry and every system's work
+ * at exit.  Returns TVR_OK if every problem converged, else the first error
+ * status, else TVR_NOT_CONVERGED.  Not an entry of the paper: a batching of
+ * its methods over problems.
+ */
+TVR_API int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t method,
+                            const float *const *bs, const double *alphas, double tau, double eps,
+                            const tvr_solve_opts *opts, float *const *xs, tvr_solve_info *infos,
+                            void *stream);
+
+/*
  * Parameter sweep: k <= 8 solves of the same system and data b with
  * regularisation parameters alphas[0..k-1] (same tau, eps and options), run in
  * lockstep so that every forward and back projection reads A once for all of

@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import (TVR_CONE, TVR_NOT_CONVERGED, TVR_OK, TVR_PARALLEL, TVR_STOP_PER_N, TVR_STOP_REL,
                     TVRError, check, lib)
 
-__all__ = ["System", "SolveOptions", "SolveResult", "project_Q", "TVRError", "lib",
+__all__ = ["System", "SolveOptions", "SolveResult", "project_Q", "solve_batch", "TVRError", "lib",
            "TVR_STOP_REL", "TVR_STOP_PER_N"]
 
 
@@ -268,6 +268,31 @@ class System:
         check(lib().tvr_profile_read(self._h, ctypes.cast(counts, ctypes.c_void_p),
                                      ctypes.cast(ms, ctypes.c_void_p)), "tvr_profile_read")
         return {"forward": (counts[0], ms[0]), "backward": (counts[1], ms[1])}
+
+
+def solve_batch(method: str, systems, bs, alphas, tau: float, eps: float, xs,
+                opts: SolveOptions | None = None, stream=None):
+    """Solve independent problems concurrently (one stream per system); list of results."""
+    code = {"gp": 1, "gpbb": 2, "upn": 3}[method]
+    n = len(systems)
+    if not (len(bs) == len(xs) == len(alphas) == n):
+        raise ValueError("systems, bs, alphas and xs must have the same length")
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in systems])
+    pb = (ctypes.c_void_p * n)(*[_ptr(b, s.m, "b")[0].value for b, s in zip(bs, systems)])
+    px = (ctypes.c_void_p * n)(*[_ptr(x, s.N, "x")[0].value for x, s in zip(xs, systems)])
+    al = (ctypes.c_double * n)(*[float(a) for a in alphas])
+    co = systems[0]._opts(opts)
+    infos = (_capi.SolveInfo * n)()
+    st = lib().tvr_solve_batch(ctypes.cast(hs, ctypes.c_void_p), n, code,
+                               ctypes.cast(pb, ctypes.c_void_p), ctypes.cast(al, ctypes.c_void_p),
+                               float(tau), float(eps), ctypes.byref(co),
+                               ctypes.cast(px, ctypes.c_void_p), infos,
+                               _stream(stream, *bs, *xs))
+    check(st, "tvr_solve_batch", allow=(TVR_OK, TVR_NOT_CONVERGED))
+    return [SolveResult(status=i.status, iters=i.iters, f_evals=i.f_evals, g_evals=i.g_evals,
+                        trials=i.trials, passes=i.passes, phi=i.phi, gnorm=i.gnorm,
+                        gnorm0=i.gnorm0, stop_value=i.stop_value, L=i.L, theta=i.theta, mu=i.mu)
+            for i in infos]
 
 
 def project_Q(x, stream=None):

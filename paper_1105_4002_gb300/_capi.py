@@ -76,6 +76,8 @@ SIGNATURES = {
                                       ctypes.POINTER(SolveInfo), _P]),
     "tvr_solve_upn": (ctypes.c_int, [_P, _P, _D, _D, _D, ctypes.POINTER(SolveOpts), _P,
                                      ctypes.POINTER(SolveInfo), _P]),
+    "tvr_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _D, _D,
+                                       ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo), _P]),
     "tvr_solve_sweep": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _D, _D,
                                        ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo), _P]),
     "tvr_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),

@@ -77,6 +77,7 @@ int tvr_system_free(tvr_system *sys) {
   for (auto &g : sys->pass_graph)
     if (g) cudaGraphExecDestroy(g);
   if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
+  if (sys->run_stream) cudaStreamDestroy(sys->run_stream);
   for (int k = 0; k < 2; ++k)
     for (int i = 0; i < kProfPairs; ++i)
       for (int w = 0; w < 2; ++w)

@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "system.cuh"
 
@@ -66,15 +67,24 @@ int pass_graph(tvr_system *sys, int solver, int batch, cudaGraphExec_t *out) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-int solve(const tvr_system *csys, int solver, const float *b, double alpha, double tau, double eps,
-          const tvr_solve_opts *uo, float *x, tvr_solve_info *info, void *stream) {
-  tvr_system *sys = const_cast<tvr_system *>(csys);
-  if (!sys || !b || !x) return fail(TVR_ERR_ARG, "tvr_solve: null argument");
-  if (!(alpha >= 0.0) || !std::isfinite(alpha) || !finite_pos(tau) || !finite_pos(eps))
-    return fail(TVR_ERR_ARG, "tvr_solve: need alpha >= 0, tau > 0, eps > 0 (finite)");
-  tvr_solve_opts o;
-  tvr_solve_opts_default(&o);
-  if (uo) o = *uo;
+// One solve, split into phases so that several solves can interleave on
+// their own streams (tvr_solve_batch).
+struct Job {
+  tvr_system *sys = nullptr;
+  int solver = 0;
+  double alpha = 0, tau = 0, eps = 0;
+  tvr_solve_opts o{};
+  float *x = nullptr;
+  bool xdev = false;
+  const float *bd = nullptr;
+  int64_t hist_n = 0;
+  cudaStream_t s = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t passes = 0, max_passes = 0;
+  bool done = false;
+};
+
+int check_opts(const tvr_solve_opts &o) {
   if (o.k_max < 1 || o.gpbb_K < 0 || o.gpbb_K > 8 || o.gpbb_max_trials < 0 || o.bt_max < 0 ||
       o.batch < 1 || o.batch > 1024 || !(o.rho_L > 1.0) || !std::isfinite(o.rho_L) ||
       !finite_pos(o.L_bar) || !(o.mu_bar >= 0.0) || !std::isfinite(o.mu_bar) ||
@@ -82,14 +92,31 @@ int solve(const tvr_system *csys, int solver, const float *b, double alpha, doub
       (o.stop_mode != TVR_STOP_REL && o.stop_mode != TVR_STOP_PER_N) || o.history_len < 0 ||
       (o.history_len > 0 && !o.history))
     return fail(TVR_ERR_ARG, "tvr_solve: invalid options");
-  const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t s = (cudaStream_t)stream;
-  const int64_t hist_n = o.history ? (o.history_len < (1 << 30) ? o.history_len : (1 << 30)) : 0;
-  if (int rc = ensure_solver(sys, hist_n)) return rc;
-  const float *bd;
-  if (int rc = stage_in(b, sys->m, &sys->stage_bM, s, &bd)) return rc;
-  const bool xdev = is_device_ptr(x);
-  const cudaMemcpyKind kin = xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  return TVR_OK;
+}
+
+// Validate, upload x0 and the state, launch the initial phi and gradient.
+int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha, double tau,
+              double eps, const tvr_solve_opts *uo, float *x, cudaStream_t s) {
+  if (!sys || !b || !x) return fail(TVR_ERR_ARG, "tvr_solve: null argument");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha) || !finite_pos(tau) || !finite_pos(eps))
+    return fail(TVR_ERR_ARG, "tvr_solve: need alpha >= 0, tau > 0, eps > 0 (finite)");
+  j.sys = sys;
+  j.solver = solver;
+  j.alpha = alpha;
+  j.tau = tau;
+  j.eps = eps;
+  j.s = s;
+  j.x = x;
+  tvr_solve_opts_default(&j.o);
+  if (uo) j.o = *uo;
+  if (int rc = check_opts(j.o)) return rc;
+  const tvr_solve_opts &o = j.o;
+  j.hist_n = o.history ? (o.history_len < (1 << 30) ? o.history_len : (1 << 30)) : 0;
+  if (int rc = ensure_solver(sys, j.hist_n)) return rc;
+  if (int rc = stage_in(b, sys->m, &sys->stage_bM, s, &j.bd)) return rc;
+  j.xdev = is_device_ptr(x);
+  const cudaMemcpyKind kin = j.xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   TVR_CUDA(cudaMemcpyAsync(sys->vN[0], x, sizeof(float) * sys->N, kin, s));
   if (solver == SOLVER_UPN) {
     TVR_CUDA(cudaMemcpyAsync(sys->vN[2], sys->vN[0], sizeof(float) * sys->N,
@@ -113,71 +140,85 @@ int solve(const tvr_system *csys, int solver, const float *b, double alpha, doub
   h.stop_mode = o.stop_mode;
   h.solver = solver;
   h.N = sys->N;
-  h.b = bd;
+  h.b = j.bd;
   for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
   for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
   h.t2 = sys->t2;
-  h.hist = hist_n > 0 ? sys->hist_dev : nullptr;
+  h.hist = j.hist_n > 0 ? sys->hist_dev : nullptr;
   h.prof_flags = sys->prof_flags_dev;
-  h.hist_cap = (int)hist_n;
+  h.hist_cap = (int)j.hist_n;
   TVR_CUDA(cudaMemcpyAsync(sys->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  const MatDev A = sys->mat();
-  launch_solver_init(A, sys->st, sys->ws, s);
+  launch_solver_init(sys->mat(), sys->st, sys->ws, s);
   TVR_CUDA(cudaGetLastError());
-
-  cudaGraphExec_t exec = nullptr;
+  j.exec = nullptr;
   if (o.use_graph && !sys->profile)
-    if (int rc = pass_graph(sys, solver, o.batch, &exec)) return rc;
+    if (int rc = pass_graph(sys, solver, o.batch, &j.exec)) return rc;
   const int64_t trials = (o.bt_max > o.gpbb_max_trials ? o.bt_max : o.gpbb_max_trials) + 2;
-  const int64_t max_passes = ((int64_t)o.k_max + 1) * trials + o.batch;
-  int64_t passes = 0;
-  bool done = false;
-  while (!done && passes < max_passes) {
-    if (exec) {
-      TVR_CUDA(cudaGraphLaunch(exec, s));
-    } else {
-      for (int i = 0; i < o.batch; ++i) {
-        PassTiming tm;
-        const PassTiming *tp = nullptr;
-        if (sys->profile) {
-          if (sys->prof_n[0] >= kProfPairs || sys->prof_n[1] >= kProfPairs)
-            if (int rc = prof_harvest(sys)) return rc;
-          const int a = prof_take(sys, 0, true), c = prof_take(sys, 1, true);
-          if (a >= 0 && c >= 0) {
-            for (int w = 0; w < 2; ++w) {
-              tm.ev[0][w] = sys->prof_ev[0][a][w];
-              tm.ev[1][w] = sys->prof_ev[1][c][w];
-            }
-            tm.slot[0] = a;
-            tm.slot[1] = c;
-            tp = &tm;
+  j.max_passes = ((int64_t)o.k_max + 1) * trials + o.batch;
+  j.passes = 0;
+  j.done = false;
+  return TVR_OK;
+}
+
+// One batch of passes and an asynchronous copy of the "done" word.
+int job_launch(Job &j) {
+  tvr_system *sys = j.sys;
+  const MatDev A = sys->mat();
+  if (j.exec) {
+    TVR_CUDA(cudaGraphLaunch(j.exec, j.s));
+  } else {
+    for (int i = 0; i < j.o.batch; ++i) {
+      PassTiming tm;
+      const PassTiming *tp = nullptr;
+      if (sys->profile) {
+        if (sys->prof_n[0] >= kProfPairs || sys->prof_n[1] >= kProfPairs)
+          if (int rc = prof_harvest(sys)) return rc;
+        const int a = prof_take(sys, 0, true), c = prof_take(sys, 1, true);
+        if (a >= 0 && c >= 0) {
+          for (int w = 0; w < 2; ++w) {
+            tm.ev[0][w] = sys->prof_ev[0][a][w];
+            tm.ev[1][w] = sys->prof_ev[1][c][w];
           }
+          tm.slot[0] = a;
+          tm.slot[1] = c;
+          tp = &tm;
         }
-        launch_solver_pass(A, sys->st, solver, sys->ws, s, tp);
       }
-      TVR_CUDA(cudaGetLastError());
+      launch_solver_pass(A, sys->st, j.solver, sys->ws, j.s, tp);
     }
-    passes += o.batch;
-    TVR_CUDA(cudaMemcpyAsync(sys->pinned_flag, &sys->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TVR_CUDA(cudaStreamSynchronize(s));
-    done = *sys->pinned_flag != 0;
+    TVR_CUDA(cudaGetLastError());
   }
+  j.passes += j.o.batch;
+  TVR_CUDA(cudaMemcpyAsync(sys->pinned_flag, &sys->st->done, sizeof(int), cudaMemcpyDeviceToHost,
+                           j.s));
+  return TVR_OK;
+}
+
+// After the job's stream has drained: read the flag.
+void job_poll(Job &j) {
+  j.done = *j.sys->pinned_flag != 0 || j.passes >= j.max_passes;
+}
+
+// Copy x*, evaluate phi(x*), copy the history, fill info.  Synchronises.
+int job_end(Job &j, tvr_solve_info *info) {
+  tvr_system *sys = j.sys;
+  cudaStream_t s = j.s;
   DevState f;
   TVR_CUDA(cudaMemcpyAsync(&f, sys->st, sizeof(f), cudaMemcpyDeviceToHost, s));
   TVR_CUDA(cudaStreamSynchronize(s));
-  const cudaMemcpyKind kout = xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  TVR_CUDA(cudaMemcpyAsync(x, f.vN[RN_X], sizeof(float) * sys->N, kout, s));
-  // phi at the returned point, evaluated afresh
-  launch_forward(A, f.vN[RN_X], bd, f.vM[RM_RT], sys->ws, s);
-  launch_tv_value(A, f.vN[RN_X], (float)alpha, (float)tau, sys->ws, sys->phi_ws, s);
+  const MatDev A = sys->mat();
+  const cudaMemcpyKind kout = j.xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  TVR_CUDA(cudaMemcpyAsync(j.x, f.vN[RN_X], sizeof(float) * sys->N, kout, s));
+  launch_forward(A, f.vN[RN_X], j.bd, f.vM[RM_RT], sys->ws, s);
+  launch_tv_value(A, f.vN[RN_X], (float)j.alpha, (float)j.tau, sys->ws, sys->phi_ws, s);
   TVR_CUDA(cudaGetLastError());
   double phi[3] = {0, 0, 0};
   TVR_CUDA(cudaMemcpyAsync(phi, sys->phi_ws, sizeof(phi), cudaMemcpyDeviceToHost, s));
   int hist_used = 0;
-  if (hist_n > 0 && f.hist_used > 0) {
+  if (j.hist_n > 0 && f.hist_used > 0) {
     hist_used = f.hist_used;
-    TVR_CUDA(cudaMemcpyAsync(o.history, sys->hist_dev, sizeof(double) * TVR_HIST_FIELDS * hist_used,
-                             cudaMemcpyDeviceToHost, s));
+    TVR_CUDA(cudaMemcpyAsync(j.o.history, sys->hist_dev,
+                             sizeof(double) * TVR_HIST_FIELDS * hist_used, cudaMemcpyDeviceToHost, s));
   }
   TVR_CUDA(cudaStreamSynchronize(s));
   const int status = f.done ? f.status : TVR_NOT_CONVERGED;
@@ -188,23 +229,36 @@ int solve(const tvr_system *csys, int solver, const float *b, double alpha, doub
     info->f_evals = f.f_evals;
     info->g_evals = f.g_evals;
     info->trials = f.total_trials;
-    info->passes = (int32_t)passes;
+    info->passes = (int32_t)j.passes;
     info->history_used = hist_used;
     info->phi = phi[0];
     info->gnorm = f.gnorm;
     info->gnorm0 = f.gnorm0;
     info->stop_value = f.stopval;
-    info->L = solver == SOLVER_GPBB ? 1.0 / f.theta : f.L;
+    info->L = j.solver == SOLVER_GPBB ? 1.0 / f.theta : f.L;
     info->theta = f.theta;
     info->mu = f.mu;
   }
-  (void)t0;
   if (status < 0) {
     const char *what = status == TVR_ERR_LINESEARCH ? "line search hit its trial cap"
                                                     : "non-finite control value";
     fail(status, std::string("tvr_solve: ") + what);
   }
   return status;
+}
+
+int solve(const tvr_system *csys, int solver, const float *b, double alpha, double tau, double eps,
+          const tvr_solve_opts *uo, float *x, tvr_solve_info *info, void *stream) {
+  Job j;
+  if (int rc = job_begin(j, const_cast<tvr_system *>(csys), solver, b, alpha, tau, eps, uo, x,
+                         (cudaStream_t)stream))
+    return rc;
+  while (!j.done) {
+    if (int rc = job_launch(j)) return rc;
+    TVR_CUDA(cudaStreamSynchronize(j.s));
+    job_poll(j);
+  }
+  return job_end(j, info);
 }
 
 }  // namespace
@@ -224,6 +278,54 @@ int tvr_solve_gpbb(const tvr_system *sys, const float *b, double alpha, double t
 int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, double tau, double eps,
                   const tvr_solve_opts *opts, float *x, tvr_solve_info *info, void *stream) {
   return solve(sys, SOLVER_UPN, b, alpha, tau, eps, opts, x, info, stream);
+}
+
+int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t method,
+                    const float *const *bs, const double *alphas, double tau, double eps,
+                    const tvr_solve_opts *opts, float *const *xs, tvr_solve_info *infos,
+                    void *stream) {
+  if (!systems || !bs || !alphas || !xs || count < 1)
+    return fail(TVR_ERR_ARG, "tvr_solve_batch: null argument or count < 1");
+  if (method != SOLVER_GP && method != SOLVER_GPBB && method != SOLVER_UPN)
+    return fail(TVR_ERR_ARG, "tvr_solve_batch: method must be 1 (GP), 2 (GPBB) or 3 (UPN)");
+  for (int i = 0; i < count; ++i) {
+    if (!systems[i]) return fail(TVR_ERR_ARG, "tvr_solve_batch: null system");
+    for (int k = 0; k < i; ++k)
+      if (systems[k] == systems[i])
+        return fail(TVR_ERR_ARG, "tvr_solve_batch: a system appears twice (they share workspace)");
+  }
+  TVR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));  // inputs written on the caller's stream
+  std::vector<Job> jobs(count);
+  for (int i = 0; i < count; ++i) {
+    tvr_system *sys = systems[i];
+    if (!sys->run_stream) TVR_CUDA(cudaStreamCreateWithFlags(&sys->run_stream, cudaStreamNonBlocking));
+    if (int rc = job_begin(jobs[i], sys, method, bs[i], alphas[i], tau, eps, opts, xs[i],
+                           sys->run_stream))
+      return rc;
+  }
+  // interleave: every unfinished problem gets a batch of passes on its own
+  // stream, then the host reads all flags
+  for (;;) {
+    bool all = true;
+    for (auto &j : jobs)
+      if (!j.done) {
+        if (int rc = job_launch(j)) return rc;
+        all = false;
+      }
+    if (all) break;
+    for (auto &j : jobs)
+      if (!j.done) {
+        TVR_CUDA(cudaStreamSynchronize(j.s));
+        job_poll(j);
+      }
+  }
+  int worst = TVR_OK;
+  for (int i = 0; i < count; ++i) {
+    const int st = job_end(jobs[i], infos ? &infos[i] : nullptr);
+    if (st < 0 && worst >= 0) worst = st;
+    if (st == TVR_NOT_CONVERGED && worst == TVR_OK) worst = st;
+  }
+  return worst;
 }
 
 }  // extern "C"

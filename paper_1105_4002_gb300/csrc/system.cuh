@@ -44,6 +44,7 @@ struct tvr_system {
   int hist_cap = 0;
   int *pinned_flag = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t run_stream = nullptr;  // stream of this system's solve inside a batch
   cudaGraphExec_t pass_graph[4] = {};
   int pass_graph_batch[4] = {};
   // kernel timing: event pairs of launches not yet harvested; a pair counts
