@@ -308,7 +308,10 @@ TVR_API int tvr_solve_sweep(const tvr_system *sys, int32_t method, const float *
                             void *stream);
 
 /*
- * Kernel timing for measurement: while enabled, the library records a CUDA
+ * Kernel timing for measurement: bits 0-3 of `enable` select the kernel kinds
+ * to time (0 = off, 1 = forward only, 15 = all); bits 8-15 give a sampling
+ * stride for solves replayed as pass graphs (time every stride-th pass of a
+ * batch; 0 or 1 = every pass).  While enabled, the library records a CUDA
  * event pair on the launch stream around every forward (CSR) and back (CSC +
  * TV) projection kernel launched outside a CUDA graph.  tvr_profile_read
  * synchronises those events and returns, per kernel kind (0 = forward,
@@ -316,7 +319,7 @@ TVR_API int tvr_solve_sweep(const tvr_system *sys, int32_t method, const float *
  * milliseconds (host outputs), then resets the counters.
  */
 TVR_API int tvr_profile_enable(tvr_system *sys, int32_t enable);
-TVR_API int tvr_profile_read(tvr_system *sys, int64_t counts[2], double total_ms[2]);
+TVR_API int tvr_profile_read(tvr_system *sys, int64_t counts[4], double total_ms[4]);
 
 /* Name of a status code. */
 TVR_API const char *tvr_status_str(int status);

@@ -259,15 +259,23 @@ class System:
         return co
 
     # ---- measurement ----
-    def profile(self, enable: bool):
-        check(lib().tvr_profile_enable(self._h, 1 if enable else 0), "tvr_profile_enable")
+    def profile(self, enable, kinds=("forward", "backward", "step", "extrapolation"),
+                sample_stride: int = 1):
+        """Time launches of the given kernel kinds (enable=False: stop timing);
+        solves in graph mode time every sample_stride-th pass."""
+        names = ["forward", "backward", "step", "extrapolation"]
+        mask = sum(1 << names.index(k) for k in kinds) if enable else 0
+        if enable:
+            mask |= (int(sample_stride) & 0xff) << 8
+        check(lib().tvr_profile_enable(self._h, mask), "tvr_profile_enable")
 
     def profile_read(self):
-        counts = (ctypes.c_int64 * 2)()
-        ms = (ctypes.c_double * 2)()
+        counts = (ctypes.c_int64 * 4)()
+        ms = (ctypes.c_double * 4)()
         check(lib().tvr_profile_read(self._h, ctypes.cast(counts, ctypes.c_void_p),
                                      ctypes.cast(ms, ctypes.c_void_p)), "tvr_profile_read")
-        return {"forward": (counts[0], ms[0]), "backward": (counts[1], ms[1])}
+        return {"forward": (counts[0], ms[0]), "backward": (counts[1], ms[1]),
+                "step": (counts[2], ms[2]), "extrapolation": (counts[3], ms[3])}
 
 
 def solve_batch(method: str, systems, bs, alphas, tau: float, eps: float, xs,

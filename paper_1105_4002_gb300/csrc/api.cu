@@ -76,9 +76,15 @@ int tvr_system_free(tvr_system *sys) {
   cudaDeviceSynchronize();
   for (auto &g : sys->pass_graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto &g : sys->pass_graph_prof)
+    if (g) cudaGraphExecDestroy(g);
+  if (sys->gprof_ev) {
+    for (int i = 0; i < sys->gprof_batch * TVR_PROF_KINDS * 2; ++i) cudaEventDestroy(sys->gprof_ev[i]);
+    delete[] sys->gprof_ev;
+  }
   if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
   if (sys->run_stream) cudaStreamDestroy(sys->run_stream);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < TVR_PROF_KINDS; ++k)
     for (int i = 0; i < kProfPairs; ++i)
       for (int w = 0; w < 2; ++w)
         if (sys->prof_ev[k][i][w]) cudaEventDestroy(sys->prof_ev[k][i][w]);
@@ -412,23 +418,25 @@ void tvr_solve_opts_default(tvr_solve_opts *o) {
 int tvr_profile_enable(tvr_system *sys, int32_t enable) {
   if (!sys) return fail(TVR_ERR_ARG, "tvr_profile_enable: null system");
   if (enable && !sys->prof_ev[0][0][0]) {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < TVR_PROF_KINDS; ++k)
       for (int i = 0; i < kProfPairs; ++i)
         for (int w = 0; w < 2; ++w) TVR_CUDA(cudaEventCreate(&sys->prof_ev[k][i][w]));
-    TVR_CUDA(cudaMalloc(&sys->prof_flags_dev, sizeof(int) * 2 * kProfPairs));
-    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * 2 * kProfPairs));
-    TVR_CUDA(cudaMallocHost(&sys->prof_flags_host, sizeof(int) * 2 * kProfPairs));
+    TVR_CUDA(cudaMalloc(&sys->prof_flags_dev, sizeof(int) * TVR_PROF_KINDS * kProfPairs));
+    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * TVR_PROF_KINDS * kProfPairs));
+    TVR_CUDA(cudaMallocHost(&sys->prof_flags_host, sizeof(int) * TVR_PROF_KINDS * kProfPairs));
   }
-  if (!enable && sys->profile)
+  if (sys->profile)
     if (int rc = prof_harvest(sys)) return rc;
-  sys->profile = enable ? 1 : 0;
+  sys->profile = enable & ((1 << TVR_PROF_KINDS) - 1);
+  const int stride = (enable >> 8) & 0xff;
+  sys->prof_stride = stride > 0 ? stride : 1;
   return TVR_OK;
 }
 
-int tvr_profile_read(tvr_system *sys, int64_t counts[2], double total_ms[2]) {
+int tvr_profile_read(tvr_system *sys, int64_t counts[4], double total_ms[4]) {
   if (!sys || !counts || !total_ms) return fail(TVR_ERR_ARG, "tvr_profile_read: null argument");
   if (int rc = prof_harvest(sys)) return rc;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < TVR_PROF_KINDS; ++k) {
     counts[k] = sys->prof_cnt[k];
     total_ms[k] = sys->prof_ms[k];
     sys->prof_cnt[k] = 0;

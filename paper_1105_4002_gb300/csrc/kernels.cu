@@ -359,8 +359,11 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
 // recomputed with the same expression, so the TV Bregman sum sees exactly the
 // stored values.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK) k_step(MatDev A, RedSlot slot, DevState *st) {
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_step(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
   if (st->done) return;
+  if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
+    st->prof_flags[2 * TVR_PROF_PAIRS + prof_slot] = 1;
   const bool upn = st->solver == SOLVER_UPN;
   const float *__restrict__ p = upn ? st->vN[RN_Y] : st->vN[RN_X];
   const float *__restrict__ g = st->vN[RN_G];
@@ -420,8 +423,11 @@ __global__ void __launch_bounds__(TVR_BLOCK) k_step(MatDev A, RedSlot slot, DevS
 //   A y - b = (A x+ - b) + beta u,
 // so the residual at y needs no projection.  Reductions: ||x+ - x||^2, ||u||^2.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK) k_yform(MatDev A, RedSlot slot, DevState *st) {
+__global__ void __launch_bounds__(TVR_BLOCK)
+    k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
   if (st->done || !st->need_grad) return;
+  if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
+    st->prof_flags[3 * TVR_PROF_PAIRS + prof_slot] = 1;
   const float beta = (float)st->beta, bp = (float)st->beta_prev;
   const float *__restrict__ X = st->vN[RN_X];
   const float *__restrict__ T = st->vN[RN_T];
@@ -601,16 +607,30 @@ void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cuda
 // rejected trial) -> projected trial step -> forward projection + test.
 void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
                         cudaStream_t s, const PassTiming *tm) {
-  if (solver == SOLVER_UPN)
-    k_yform<<<elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.yf, st);
-  if (tm) cudaEventRecord(tm->ev[1][0], s);
+  auto mark = [&](int kind, int which) {
+    if (!tm || tm->slot[kind] < 0) return;
+    if (tm->graph_nodes)
+      cudaEventRecordWithFlags(tm->ev[kind][which], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(tm->ev[kind][which], s);
+  };
+  auto slot = [&](int kind) { return tm ? tm->slot[kind] : -1; };
+  if (solver == SOLVER_UPN) {
+    mark(3, 0);
+    k_yform<<<elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.yf, st,
+                                                                             slot(3));
+    mark(3, 1);
+  }
+  mark(1, 0);
   bwd_kernel<BWD_SOLVER>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st,
-      tm ? tm->slot[1] : -1, nullptr, nullptr);
-  if (tm) cudaEventRecord(tm->ev[1][1], s);
-  k_step<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.step, st);
-  if (tm) cudaEventRecord(tm->ev[0][0], s);
-  fwd_kernel<FWD_TRIAL>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(
-      A, nullptr, nullptr, nullptr, ws.fwd, st, tm ? tm->slot[0] : -1, nullptr);
-  if (tm) cudaEventRecord(tm->ev[0][1], s);
+      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st, slot(1), nullptr,
+      nullptr);
+  mark(1, 1);
+  mark(2, 0);
+  k_step<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.step, st, slot(2));
+  mark(2, 1);
+  mark(0, 0);
+  fwd_kernel<FWD_TRIAL>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr, ws.fwd,
+                                                              st, slot(0), nullptr);
+  mark(0, 1);
 }

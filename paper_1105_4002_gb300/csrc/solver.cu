@@ -40,18 +40,58 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
   return TVR_OK;
 }
 
-int pass_graph(tvr_system *sys, int solver, int batch, cudaGraphExec_t *out) {
-  if (sys->pass_graph[solver] && sys->pass_graph_batch[solver] == batch) {
-    *out = sys->pass_graph[solver];
+// A batch of passes captured once per (system, method, batch size) and
+// replayed.  With kernel timing on, the graph also holds an event node pair
+// around every kernel and gives each pass its slot for the "did work" flags.
+int pass_graph(tvr_system *sys, int solver, int batch, bool timed, cudaGraphExec_t *out) {
+  cudaGraphExec_t &cache = timed ? sys->pass_graph_prof[solver] : sys->pass_graph[solver];
+  int &cache_batch = timed ? sys->pass_graph_prof_batch[solver] : sys->pass_graph_batch[solver];
+  const int key = sys->profile | (sys->prof_stride << 8);
+  if (cache && cache_batch == batch && (!timed || sys->pass_graph_prof_mask[solver] == key)) {
+    *out = cache;
     return TVR_OK;
   }
-  if (sys->pass_graph[solver]) {
-    cudaGraphExecDestroy(sys->pass_graph[solver]);
-    sys->pass_graph[solver] = nullptr;
+  if (cache) {
+    cudaGraphExecDestroy(cache);
+    cache = nullptr;
+  }
+  if (timed && sys->gprof_batch < batch) {
+    if (sys->gprof_ev) {
+      for (int i = 0; i < sys->gprof_batch * TVR_PROF_KINDS * 2; ++i)
+        cudaEventDestroy(sys->gprof_ev[i]);
+      delete[] sys->gprof_ev;
+      sys->gprof_ev = nullptr;
+      sys->gprof_batch = 0;
+      // graphs recorded with the old events are stale
+      for (auto &g : sys->pass_graph_prof)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+    }
+    sys->gprof_ev = new cudaEvent_t[(size_t)batch * TVR_PROF_KINDS * 2]();
+    for (int i = 0; i < batch * TVR_PROF_KINDS * 2; ++i)
+      TVR_CUDA(cudaEventCreate(&sys->gprof_ev[i]));
+    sys->gprof_batch = batch;
   }
   const MatDev A = sys->mat();
   TVR_CUDA(cudaStreamBeginCapture(sys->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < batch; ++i) launch_solver_pass(A, sys->st, solver, sys->ws, sys->cap_stream);
+  for (int i = 0; i < batch; ++i) {
+    if (timed) {
+      PassTiming tm;
+      tm.graph_nodes = true;
+      for (int k = 0; k < TVR_PROF_KINDS; ++k) {
+        tm.slot[k] = ((k != 3 || solver == SOLVER_UPN) && ((sys->profile >> k) & 1) &&
+                      i % sys->prof_stride == 0)
+                         ? i
+                         : -1;
+        for (int w = 0; w < 2; ++w) tm.ev[k][w] = sys->gprof_ev[(i * TVR_PROF_KINDS + k) * 2 + w];
+      }
+      launch_solver_pass(A, sys->st, solver, sys->ws, sys->cap_stream, &tm);
+    } else {
+      launch_solver_pass(A, sys->st, solver, sys->ws, sys->cap_stream);
+    }
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(sys->cap_stream, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(pass batch)");
@@ -59,9 +99,28 @@ int pass_graph(tvr_system *sys, int solver, int batch, cudaGraphExec_t *out) {
   e = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(pass batch)");
-  sys->pass_graph[solver] = exec;
-  sys->pass_graph_batch[solver] = batch;
+  cache = exec;
+  cache_batch = batch;
+  if (timed) sys->pass_graph_prof_mask[solver] = key;
   *out = exec;
+  return TVR_OK;
+}
+
+// After a replay of a timed pass graph has completed: add the durations of
+// the launches that did work, then clear their flags.
+int graph_prof_harvest(tvr_system *sys, int batch) {
+  const size_t bytes = sizeof(int) * TVR_PROF_KINDS * kProfPairs;
+  TVR_CUDA(cudaMemcpy(sys->prof_flags_host, sys->prof_flags_dev, bytes, cudaMemcpyDeviceToHost));
+  TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, bytes));
+  for (int i = 0; i < batch; ++i)
+    for (int k = 0; k < TVR_PROF_KINDS; ++k) {
+      if (!sys->prof_flags_host[k * kProfPairs + i]) continue;
+      float ms = 0.f;
+      TVR_CUDA(cudaEventElapsedTime(&ms, sys->gprof_ev[(i * TVR_PROF_KINDS + k) * 2],
+                                    sys->gprof_ev[(i * TVR_PROF_KINDS + k) * 2 + 1]));
+      sys->prof_ms[k] += ms;
+      sys->prof_cnt[k] += 1;
+    }
   return TVR_OK;
 }
 
@@ -80,6 +139,7 @@ struct Job {
   int64_t hist_n = 0;
   cudaStream_t s = nullptr;
   cudaGraphExec_t exec = nullptr;
+  bool timed_graph = false;
   int64_t passes = 0, max_passes = 0;
   bool done = false;
 };
@@ -151,8 +211,9 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   launch_solver_init(sys->mat(), sys->st, sys->ws, s);
   TVR_CUDA(cudaGetLastError());
   j.exec = nullptr;
-  if (o.use_graph && !sys->profile)
-    if (int rc = pass_graph(sys, solver, o.batch, &j.exec)) return rc;
+  j.timed_graph = o.use_graph && sys->profile && o.batch <= kProfPairs;
+  if (o.use_graph && (!sys->profile || j.timed_graph))
+    if (int rc = pass_graph(sys, solver, o.batch, j.timed_graph, &j.exec)) return rc;
   const int64_t trials = (o.bt_max > o.gpbb_max_trials ? o.bt_max : o.gpbb_max_trials) + 2;
   j.max_passes = ((int64_t)o.k_max + 1) * trials + o.batch;
   j.passes = 0;
@@ -171,18 +232,18 @@ int job_launch(Job &j) {
       PassTiming tm;
       const PassTiming *tp = nullptr;
       if (sys->profile) {
-        if (sys->prof_n[0] >= kProfPairs || sys->prof_n[1] >= kProfPairs)
+        bool full = false;
+        for (int k = 0; k < TVR_PROF_KINDS; ++k) full = full || sys->prof_n[k] >= kProfPairs;
+        if (full)
           if (int rc = prof_harvest(sys)) return rc;
-        const int a = prof_take(sys, 0, true), c = prof_take(sys, 1, true);
-        if (a >= 0 && c >= 0) {
-          for (int w = 0; w < 2; ++w) {
-            tm.ev[0][w] = sys->prof_ev[0][a][w];
-            tm.ev[1][w] = sys->prof_ev[1][c][w];
-          }
-          tm.slot[0] = a;
-          tm.slot[1] = c;
-          tp = &tm;
+        for (int k = 0; k < TVR_PROF_KINDS; ++k) {
+          const bool used = (k != 3 || j.solver == SOLVER_UPN) && ((sys->profile >> k) & 1);
+          const int sl = used ? prof_take(sys, k, true) : -1;
+          tm.slot[k] = sl;
+          if (sl >= 0)
+            for (int w = 0; w < 2; ++w) tm.ev[k][w] = sys->prof_ev[k][sl][w];
         }
+        tp = &tm;
       }
       launch_solver_pass(A, sys->st, j.solver, sys->ws, j.s, tp);
     }
@@ -194,9 +255,12 @@ int job_launch(Job &j) {
   return TVR_OK;
 }
 
-// After the job's stream has drained: read the flag.
-void job_poll(Job &j) {
+// After the job's stream has drained: read the flag (and the kernel timings).
+int job_poll(Job &j) {
   j.done = *j.sys->pinned_flag != 0 || j.passes >= j.max_passes;
+  if (j.timed_graph)
+    if (int rc = graph_prof_harvest(j.sys, j.o.batch)) return rc;
+  return TVR_OK;
 }
 
 // Copy x*, evaluate phi(x*), copy the history, fill info.  Synchronises.
@@ -256,7 +320,7 @@ int solve(const tvr_system *csys, int solver, const float *b, double alpha, doub
   while (!j.done) {
     if (int rc = job_launch(j)) return rc;
     TVR_CUDA(cudaStreamSynchronize(j.s));
-    job_poll(j);
+    if (int rc = job_poll(j)) return rc;
   }
   return job_end(j, info);
 }
@@ -316,7 +380,7 @@ int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t method,
     for (auto &j : jobs)
       if (!j.done) {
         TVR_CUDA(cudaStreamSynchronize(j.s));
-        job_poll(j);
+        if (int rc = job_poll(j)) return rc;
       }
   }
   int worst = TVR_OK;

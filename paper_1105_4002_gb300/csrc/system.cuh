@@ -47,16 +47,23 @@ struct tvr_system {
   cudaStream_t run_stream = nullptr;  // stream of this system's solve inside a batch
   cudaGraphExec_t pass_graph[4] = {};
   int pass_graph_batch[4] = {};
+  // the same pass graphs with event nodes around every kernel (kernel timing)
+  cudaGraphExec_t pass_graph_prof[4] = {};
+  int pass_graph_prof_batch[4] = {};
+  int pass_graph_prof_mask[4] = {};  // profile | prof_stride << 8 the graph was captured with
+  cudaEvent_t *gprof_ev = nullptr;  // [gprof_batch][TVR_PROF_KINDS][2]
+  int gprof_batch = 0;
   // kernel timing: event pairs of launches not yet harvested; a pair counts
   // if it was a plain launch or if its kernel set its device "did work" flag
-  int profile = 0;
-  cudaEvent_t prof_ev[2][kProfPairs][2] = {};
-  int prof_n[2] = {0, 0};
-  int prof_slot[2][kProfPairs] = {};   // -1: plain launch, else device flag slot
-  int *prof_flags_dev = nullptr;       // [2 * kProfPairs]
-  int *prof_flags_host = nullptr;      // pinned copy
-  double prof_ms[2] = {0.0, 0.0};
-  int64_t prof_cnt[2] = {0, 0};
+  int profile = 0;      // bit k set: launches of kind k are timed
+  int prof_stride = 1;  // pass graphs: time passes i with i % prof_stride == 0
+  cudaEvent_t prof_ev[TVR_PROF_KINDS][kProfPairs][2] = {};
+  int prof_n[TVR_PROF_KINDS] = {};
+  int prof_slot[TVR_PROF_KINDS][kProfPairs] = {};  // -1: plain launch, else device flag slot
+  int *prof_flags_dev = nullptr;                   // [TVR_PROF_KINDS * kProfPairs]
+  int *prof_flags_host = nullptr;                  // pinned copy
+  double prof_ms[TVR_PROF_KINDS] = {};
+  int64_t prof_cnt[TVR_PROF_KINDS] = {};
 
   MatDev mat() const {
     MatDev d;
@@ -113,16 +120,16 @@ inline int stage_in(const float *src, int64_t len, float **stage, cudaStream_t s
 // the recorded events.
 inline int prof_harvest(tvr_system *sys) {
   bool dev = false;
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < TVR_PROF_KINDS; ++k)
     for (int i = 0; i < sys->prof_n[k]; ++i) dev = dev || sys->prof_slot[k][i] >= 0;
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < TVR_PROF_KINDS; ++k)
     if (sys->prof_n[k] > 0) TVR_CUDA(cudaEventSynchronize(sys->prof_ev[k][sys->prof_n[k] - 1][1]));
   if (dev) {
-    TVR_CUDA(cudaMemcpy(sys->prof_flags_host, sys->prof_flags_dev, sizeof(int) * 2 * kProfPairs,
+    TVR_CUDA(cudaMemcpy(sys->prof_flags_host, sys->prof_flags_dev, sizeof(int) * TVR_PROF_KINDS * kProfPairs,
                         cudaMemcpyDeviceToHost));
-    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * 2 * kProfPairs));
+    TVR_CUDA(cudaMemset(sys->prof_flags_dev, 0, sizeof(int) * TVR_PROF_KINDS * kProfPairs));
   }
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < TVR_PROF_KINDS; ++k) {
     for (int i = 0; i < sys->prof_n[k]; ++i) {
       const int sl = sys->prof_slot[k][i];
       if (sl >= 0 && !sys->prof_flags_host[k * kProfPairs + sl]) continue;
@@ -139,14 +146,14 @@ inline int prof_harvest(tvr_system *sys) {
 // Next event pair of kind k (-1 when profiling is off or the pool is full;
 // callers harvest at points where no taken pair is still unrecorded).
 inline int prof_take(tvr_system *sys, int k, bool device_flag) {
-  if (!sys->profile || sys->prof_n[k] >= kProfPairs) return -1;
+  if (!((sys->profile >> k) & 1) || sys->prof_n[k] >= kProfPairs) return -1;
   const int i = sys->prof_n[k]++;
   sys->prof_slot[k][i] = device_flag ? i : -1;
   return i;
 }
 
 inline void prof_mark(tvr_system *sys, int kind, int which, cudaStream_t s) {
-  if (!sys->profile) return;
+  if (!((sys->profile >> kind) & 1)) return;
   if (which == 0) {
     if (sys->prof_n[kind] >= kProfPairs) prof_harvest(sys);
     const int i = prof_take(sys, kind, false);

@@ -11,6 +11,7 @@
 #define TVR_RMAX 4             // reductions carried by one kernel
 #define TVR_MAX_GRID 4096      // upper bound on blocks of a reducing kernel
 #define TVR_PROF_PAIRS 4096    // timed launches held per kernel kind between harvests
+#define TVR_PROF_KINDS 4       // forward, back projection, step, UPN extrapolation
 
 // ---------------------------------------------------------------------------
 // Double-single ("float-float") accumulation.
@@ -257,7 +258,7 @@ struct DevState {
   double *hist;
   int hist_cap, hist_used;
   // kernel-timing flags: prof_flags[kind * TVR_PROF_PAIRS + slot] = 1 when a
-  // timed launch did work (kind 0 forward, 1 back projection)
+  // timed launch did work (kind 0 forward, 1 back projection, 2 step, 3 extrapolation)
   int *prof_flags;
 };
 
@@ -313,12 +314,13 @@ void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, cons
 
 // Solver-mode launchers (pointers and scalars come from the device state).
 void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s);
-// Optional CUDA-event timing of the forward (kind 0) and back projection
-// (kind 1) launches of one pass: events recorded around each launch, and the
-// launch's slot for its "did work" flag.
+// Optional CUDA-event timing of the launches of one pass (kinds: 0 forward,
+// 1 back projection, 2 step, 3 extrapolation): events recorded around each
+// launch, and the launch's slot for its "did work" flag (-1: not timed).
 struct PassTiming {
-  cudaEvent_t ev[2][2];
-  int slot[2];
+  cudaEvent_t ev[TVR_PROF_KINDS][2];
+  int slot[TVR_PROF_KINDS];
+  bool graph_nodes = false;  // record as event nodes of a graph being captured
 };
 void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
                         cudaStream_t s, const PassTiming *timing = nullptr);

@@ -98,6 +98,24 @@ def test_graph_and_direct_launches_agree_bitwise(c32):
     assert np.array_equal(x1, x2) and r1.iters == r2.iters and r1.gnorm == r2.gnorm
 
 
+def test_kernel_timing_in_graph_and_direct_modes(c32):
+    """Timed solves give the same result; every working launch is timed once."""
+    torch, s, prob, cfg = c32
+    r0, x0 = gpu_solve(c32, "upn")
+    for graph in (True, False):
+        s.profile(True)
+        s.profile_read()
+        r, x = gpu_solve(c32, "upn", use_graph=graph)
+        p = s.profile_read()
+        s.profile(False)
+        assert np.array_equal(x, x0) and r.iters == r0.iters
+        assert p["forward"][0] == r.f_evals - 1              # one trial forward per f-eval after init
+        assert p["backward"][0] == r.g_evals - 1             # one back projection per new point
+        assert p["step"][0] == r.f_evals - 1
+        assert p["extrapolation"][0] == r.g_evals - 1
+        assert all(ms > 0 for _, ms in p.values())
+
+
 def test_solves_are_deterministic(c32):
     r1, x1 = gpu_solve(c32, "gpbb")
     r2, x2 = gpu_solve(c32, "gpbb")
