@@ -25,7 +25,8 @@ int tvr_cuda_fail(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? TVR_ERR_OOM : TVR_ERR_CUDA;
 }
 
-// Copy a padded compressed layout to host and drop the padding entries.
+// Copy a padded compressed layout to host, undo the lane-interleaved stored
+// order (lane_stored) and drop the padding entries.
 static int export_compact(const int64_t *ptr_d, const int32_t *len_d, const int32_t *idx_d,
                           const float *val_d, int64_t rows, int64_t stored, int64_t *ptr_out,
                           int32_t *idx_out, float *val_out) {
@@ -43,9 +44,11 @@ static int export_compact(const int64_t *ptr_d, const int32_t *len_d, const int3
   int64_t o = 0;
   if (ptr_out) ptr_out[0] = 0;
   for (int64_t i = 0; i < rows; ++i) {
+    const int64_t L = ptr[i + 1] - ptr[i];
     for (int32_t k = 0; k < len[i]; ++k) {
-      if (idx_out) idx_out[o + k] = idx[ptr[i] + k];
-      if (val_out) val_out[o + k] = val[ptr[i] + k];
+      const int64_t e = ptr[i] + lane_stored(k, L);
+      if (idx_out) idx_out[o + k] = idx[e];
+      if (val_out) val_out[o + k] = val[e];
     }
     o += len[i];
     if (ptr_out) ptr_out[i + 1] = o;
@@ -149,6 +152,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   BUILD_CUDA(cudaMemcpyAsync(views_dev, g->views, vbytes, cudaMemcpyHostToDevice, s));
   BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
   if (storage == TVR_STORAGE_BF16_ROWSCALE) BUILD_CUDA(quantize_bf16(sys->A, s));
+  BUILD_CUDA(interleave_lanes(sys->A, s));
   sys->nnz = sys->A.nnz;
   // reduction workspace: per slot partials + counter + outputs
   const size_t part = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;

@@ -577,6 +577,49 @@ cudaError_t quantize_bf16(MatStore &A, cudaStream_t s) {
   return cudaSuccess;
 }
 
+namespace {
+
+// out[o + p] = in[o + lane_logical(p, L)] within every segment (row or column).
+template <typename T>
+__global__ void k_interleave(const int64_t *__restrict__ ptr, int64_t nseg,
+                             const T *__restrict__ in, T *__restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nseg) return;
+  const int64_t o = ptr[c], L = ptr[c + 1] - o;
+  for (int64_t p = 0; p < L; ++p) out[o + p] = in[o + lane_logical(p, L)];
+}
+
+template <typename T>
+cudaError_t interleave(const int64_t *ptr, int64_t nseg, int64_t stored, T *&arr, cudaStream_t s) {
+  if (!arr) return cudaSuccess;
+  T *out = nullptr;
+  BM_TRY(owned(&out, stored));
+  k_interleave<T><<<blocks_for(nseg), TVR_BLOCK, 0, s>>>(ptr, nseg, arr, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(out);
+    return e;
+  }
+  cudaFree(arr);
+  arr = out;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// Final stored order (lane_logical) of every entry array, CSR and CSC; run
+// after all per-entry processing that assumes the padding at the end.
+cudaError_t interleave_lanes(MatStore &A, cudaStream_t s) {
+  BM_TRY(interleave(A.row_ptr, A.m, A.nnz_pad, A.col, s));
+  BM_TRY(interleave(A.row_ptr, A.m, A.nnz_pad, A.val, s));
+  BM_TRY(interleave(A.row_ptr, A.m, A.nnz_pad, A.qval, s));
+  BM_TRY(interleave(A.col_ptr, A.N, A.nnz_cpad, A.row, s));
+  BM_TRY(interleave(A.col_ptr, A.N, A.nnz_cpad, A.cval, s));
+  BM_TRY(interleave(A.col_ptr, A.N, A.nnz_cpad, A.qcval, s));
+  return cudaSuccess;
+}
+
 // FP32 values the kernels apply, in stored (padded) order: CSR or CSC.
 cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s) {
   if (csc)

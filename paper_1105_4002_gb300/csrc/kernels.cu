@@ -11,6 +11,8 @@
 //
 // All reductions: double-single per thread / warp / block, deterministic
 // block-ordered finish in the last block (tvr_internal.cuh).
+#include <utility>
+
 #include "ctrl.cuh"
 #include "tvr_internal.cuh"
 
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
               float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1,
               float *__restrict__ rsout = nullptr) {
+  pdl_enter();
   const float *x = xin;
   const float2 *xd = nullptr;  // trial mode: (xbar, xbar - base) per voxel
   float *r = rout;
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
                const double *__restrict__ data_in, double *phi_dev, DevState *st,
                int prof_slot = -1, const double *__restrict__ scale_p = nullptr,
                float *__restrict__ gb = nullptr) {
+  pdl_enter();
   const float *r = rin;
   const float *x = xin;
   float *g = gout;
@@ -286,9 +290,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
       if (valid && lane == 0) g[j] = s;
       continue;
     }
-    const int iz = (int)(j / nn);
-    const int iy = (int)((j - (int64_t)iz * nn) / n);
-    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    int ix, iy, iz;
+    voxel_of(A, j, ix, iy, iz);
     Huber hw;
     float c = 0.f;
     if (valid && lane < 4) {
@@ -359,8 +362,9 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
 // recomputed with the same expression, so the TV Bregman sum sees exactly the
 // stored values.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK)
+__global__ void __launch_bounds__(TVR_BLOCK, 5)
     k_step(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
+  pdl_enter();
   if (st->done) return;
   if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
     st->prof_flags[2 * TVR_PROF_PAIRS + prof_slot] = 1;
@@ -389,9 +393,8 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       const float e = __fsub_rn(pj, proj(__fsub_rn(pj, __fmul_rn(s2, gj))));
       ff_add_prod(a3, e, e);
     }
-    const int iz = (int)(j / nn);
-    const int iy = (int)((j - (int64_t)iz * nn) / n);
-    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    int ix, iy, iz;
+    voxel_of(A, j, ix, iy, iz);
     float z[3], zb[3], dl[3];
     const int64_t off[3] = {1, n, nn};
     const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
@@ -425,6 +428,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
+  pdl_enter();
   if (st->done || !st->need_grad) return;
   if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
     st->prof_flags[3 * TVR_PROF_PAIRS + prof_slot] = 1;
@@ -468,13 +472,11 @@ __global__ void __launch_bounds__(TVR_BLOCK)
     k_tv_value(MatDev A, const float *__restrict__ x, float tau, double alpha_d, RedSlot slot,
                const double *__restrict__ data_in, double *phi_dev) {
   const int n = A.n;
-  const int64_t nn = (int64_t)n * n;
   FF a0 = ff_zero();
   const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
   for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < A.N; j += stride) {
-    const int iz = (int)(j / nn);
-    const int iy = (int)((j - (int64_t)iz * nn) / n);
-    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    int ix, iy, iz;
+    voxel_of(A, j, ix, iy, iz);
     float z[3];
     diff3(x, ix, iy, iz, n, z);
     ff_add(a0, huber_h(norm3(z), tau));
@@ -540,6 +542,23 @@ void kernel_grids(Workspace &ws, int device) {
   ws.grid_elem = occupancy_grid((const void *)k_step, TVR_BLOCK, device);
 }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_enter
+// first), so that its blocks are scheduled while the predecessor drains.
+template <typename... P, typename... A>
+void launch_pdl(void (*kernel)(P...), int grid, cudaStream_t s, A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TVR_BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 // Kernel instance for the system's storage (float32 or bfloat16 values).
 template <int MODE>
 auto fwd_kernel(const MatDev &A) {
@@ -552,7 +571,7 @@ auto bwd_kernel(const MatDev &A) {
 
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
                     cudaStream_t s, float *rs) {
-  fwd_kernel<FWD_RESID>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, b, r, ws.fwd, nullptr, -1, rs);
+  launch_pdl(fwd_kernel<FWD_RESID>(A), ws.grid_fwd, s, A, x, b, r, ws.fwd, nullptr, -1, rs);
 }
 
 void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
@@ -563,9 +582,8 @@ void launch_forward_plain(const MatDev &A, const float *x, float *y, const Works
 
 void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                      float *g, const Workspace &ws, double *phi_dev, cudaStream_t s) {
-  bwd_kernel<BWD_GRAD>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, r, x, alpha, tau, (double)alpha, g, ws.bwd, ws.fwd.out, phi_dev, nullptr, -1, nullptr,
-      nullptr);
+  launch_pdl(bwd_kernel<BWD_GRAD>(A), ws.grid_bwd, s, A, r, x, alpha, tau, (double)alpha, g, ws.bwd,
+             ws.fwd.out, phi_dev, nullptr, -1, nullptr, nullptr);
 }
 
 void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
@@ -576,8 +594,8 @@ void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Works
 
 void launch_vjp(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                 const double *scale, float *gx, float *gb, const Workspace &ws, cudaStream_t s) {
-  bwd_kernel<BWD_VJP>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, r, x, alpha, tau, (double)alpha, gx, ws.bwd, nullptr, nullptr, nullptr, -1, scale, gb);
+  launch_pdl(bwd_kernel<BWD_VJP>(A), ws.grid_bwd, s, A, r, x, alpha, tau, (double)alpha, gx, ws.bwd,
+             nullptr, nullptr, nullptr, -1, scale, gb);
 }
 
 void launch_tv_value(const MatDev &A, const float *x, float alpha, float tau, const Workspace &ws,
@@ -596,11 +614,10 @@ void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, cons
 }
 
 void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
-  fwd_kernel<FWD_INIT>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr, ws.fwd,
-                                                             st, -1, nullptr);
-  bwd_kernel<BWD_INIT>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st, -1, nullptr,
-      nullptr);
+  launch_pdl(fwd_kernel<FWD_INIT>(A), ws.grid_fwd, s, A, nullptr, nullptr, nullptr, ws.fwd, st, -1,
+             nullptr);
+  launch_pdl(bwd_kernel<BWD_INIT>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
+             ws.bwd, nullptr, nullptr, st, -1, nullptr, nullptr);
 }
 
 // One pass: [UPN: extrapolation] -> gradient at the new point (skipped after a
@@ -617,20 +634,18 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
   auto slot = [&](int kind) { return tm ? tm->slot[kind] : -1; };
   if (solver == SOLVER_UPN) {
     mark(3, 0);
-    k_yform<<<elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.yf, st,
-                                                                             slot(3));
+    launch_pdl(k_yform, elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), s, A, ws.yf, st, slot(3));
     mark(3, 1);
   }
   mark(1, 0);
-  bwd_kernel<BWD_SOLVER>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
-      A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr, ws.bwd, nullptr, nullptr, st, slot(1), nullptr,
-      nullptr);
+  launch_pdl(bwd_kernel<BWD_SOLVER>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
+             ws.bwd, nullptr, nullptr, st, slot(1), nullptr, nullptr);
   mark(1, 1);
   mark(2, 0);
-  k_step<<<elem_grid(A.N, ws.grid_elem), TVR_BLOCK, 0, s>>>(A, ws.step, st, slot(2));
+  launch_pdl(k_step, elem_grid(A.N, ws.grid_elem), s, A, ws.step, st, slot(2));
   mark(2, 1);
   mark(0, 0);
-  fwd_kernel<FWD_TRIAL>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, nullptr, nullptr, nullptr, ws.fwd,
-                                                              st, slot(0), nullptr);
+  launch_pdl(fwd_kernel<FWD_TRIAL>(A), ws.grid_fwd, s, A, nullptr, nullptr, nullptr, ws.fwd, st,
+             slot(0), nullptr);
   mark(0, 1);
 }

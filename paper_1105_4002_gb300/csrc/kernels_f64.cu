@@ -118,7 +118,6 @@ __global__ void __launch_bounds__(TVR_BLOCK)
                    double *__restrict__ gb, RedSlot slot, const double *__restrict__ data_in,
                    double *phi_dev) {
   const int n = A.n;
-  const int64_t nn = (int64_t)n * n;
   const int lane = threadIdx.x & (kLanes - 1);
   const int sub = (threadIdx.x & 31) / kLanes;
   const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
@@ -139,9 +138,8 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       s = fma((double)v4.w, r[i4.w], s);
     }
     s = dgroup_sum(s);
-    const int iz = (int)(j / nn);
-    const int iy = (int)((j - (int64_t)iz * nn) / n);
-    const int ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
+    int ix, iy, iz;
+    voxel_of(A, j, ix, iy, iz);
     double w[3] = {0.0, 0.0, 0.0}, h = 0.0, c = 0.0;
     if (valid) {
       huber_d(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, w, h);

@@ -125,12 +125,6 @@ __device__ __forceinline__ void huber_s(const float *x, int ix, int iy, int iz, 
 
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
-__device__ __forceinline__ void voxel(int64_t j, int n, int &ix, int &iy, int &iz) {
-  const int64_t nn = (int64_t)n * n;
-  iz = (int)(j / nn);
-  iy = (int)((j - (int64_t)iz * nn) / n);
-  ix = (int)(j - (int64_t)iz * nn - (int64_t)iy * n);
-}
 
 // ---- projections shared by all columns ----
 template <bool TWO, bool BF>
@@ -331,7 +325,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
   if (active) {
     for (int64_t j = it.i; j < A.N; j += it.stride) {
       int ix, iy, iz;
-      voxel(j, n, ix, iy, iz);
+      voxel_of(A, j, ix, iy, iz);
       Huber h0, h1, h2, h3;
       huber_s(x, ix, iy, iz, n, tau, h0);
       huber_s(x, ix - 1, iy, iz, n, tau, h1);
@@ -404,7 +398,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
         ff_add_prod(a3, e, e);
       }
       int ix, iy, iz;
-      voxel(j, n, ix, iy, iz);
+      voxel_of(A, j, ix, iy, iz);
       const int64_t off[3] = {1, n, (int64_t)n * n};
       const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
       float z[3], zb[3], dl[3];

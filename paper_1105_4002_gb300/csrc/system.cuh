@@ -68,6 +68,8 @@ struct tvr_system {
   MatDev mat() const {
     MatDev d;
     d.n = n;
+    d.div_n = make_fastdiv((uint32_t)n);
+    d.div_nn = make_fastdiv((uint32_t)n * (uint32_t)n);
     d.m = m;
     d.N = N;
     d.nnz = A.nnz_pad;

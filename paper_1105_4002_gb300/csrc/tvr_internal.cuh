@@ -265,8 +265,30 @@ struct DevState {
 // ---------------------------------------------------------------------------
 // Device views of A and launch shapes.
 // ---------------------------------------------------------------------------
+// Unsigned division by an invariant divisor d >= 1 with a multiply-high, an
+// add and a shift (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994, Sec. 4): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (mulhi(u, m) + u) >> l, exact for
+// every u < 2^31 (the sum cannot overflow).  Voxel indices are below 2^31
+// because the stored indices are int32.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (uint64_t(1) << l) < d) ++l;
+  const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+  return FastDiv{d, (uint32_t)m, l};
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t u, const FastDiv &f) {
+  return (__umulhi(u, f.m) + u) >> f.l;
+}
+
 struct MatDev {
   int n;
+  FastDiv div_n, div_nn;   // divisors n and n^2 of the voxel index
   int64_t m, N, nnz;
   const int64_t *row_ptr;  // CSR [m+1], every row padded to a multiple of 4 entries
   const int32_t *col;      // [stored]
@@ -280,6 +302,27 @@ struct MatDev {
   const __nv_bfloat16 *qcval;  // CSC codes [stored]
   const float *rscale;         // [m]
 };
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled while its predecessor on the stream is still
+// running.  It lets its own successor do the same, then waits until the
+// predecessor has completed and its writes are visible; nothing before the
+// wait touches memory.  Without a programmatic dependency both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// (ix, iy, iz) of voxel j = ix + n (iy + n iz).
+__device__ __forceinline__ void voxel_of(const MatDev &A, int64_t j, int &ix, int &iy, int &iz) {
+  const uint32_t u = (uint32_t)j;
+  const uint32_t z = fast_div(u, A.div_nn);
+  const uint32_t rem = u - z * A.div_nn.d;
+  const uint32_t y = fast_div(rem, A.div_n);
+  iz = (int)z;
+  iy = (int)y;
+  ix = (int)(rem - y * A.div_n.d);
+}
 
 struct Workspace {
   RedSlot fwd, bwd, step, yf, tv, gmap;
@@ -329,6 +372,28 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
 // CSC are padded to multiples of 4 entries (padding: the last real index with
 // value 0) so that every lane reads 4 entries with one 16-byte load; row_len /
 // col_len keep the real counts.
+// Stored order of a padded row or column of length L (a multiple of 4).  In
+// each block of 16 entries (the last block may hold 4, 8 or 12), the 4-entry
+// group that lane l of a 4-lane group loads holds the entries l, l + g,
+// l + 2g, l + 3g of the block (g = groups in the block).  The k-th elements of
+// the four lanes' groups are then four consecutive entries, so one gather
+// instruction touches neighbouring voxels of a ray (CSR) or neighbouring
+// detector pixels of a view (CSC).  Sums over a row are unchanged up to the
+// order of the additions.
+__host__ __device__ inline int64_t lane_logical(int64_t p, int64_t L) {  // stored -> logical
+  const int64_t q = p & ~int64_t(15);
+  const int64_t g4 = (L - q) >> 2;
+  const int g = g4 < 4 ? (int)g4 : 4;
+  return q + (int64_t)g * (p & 3) + ((p & 15) >> 2);
+}
+__host__ __device__ inline int64_t lane_stored(int64_t p, int64_t L) {  // logical -> stored
+  const int64_t q = p & ~int64_t(15);
+  const int64_t g4 = (L - q) >> 2;
+  const int g = g4 < 4 ? (int)g4 : 4;
+  const int r = (int)(p & 15);
+  return q + 4 * (r % g) + r / g;
+}
+
 struct MatStore {
   int64_t m = 0, N = 0;
   int64_t nnz = 0;       // real entries
@@ -348,6 +413,7 @@ int64_t scan_tmp_len(int64_t n);
 cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
                          int64_t N, MatStore &A, cudaStream_t s);
 cudaError_t quantize_bf16(MatStore &A, cudaStream_t s);
+cudaError_t interleave_lanes(MatStore &A, cudaStream_t s);
 cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s);
 void free_matrix(MatStore &A);
 
