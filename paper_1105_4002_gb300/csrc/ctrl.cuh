@@ -106,7 +106,7 @@ __device__ __forceinline__ void ctrl_init(DevState *st, const double *tot) {
 
 // After a gradient evaluation at the newly accepted point.
 // GPBB: tot[1] = <s, g_new - g_old>, tot[2] = ||s||^2, s = x^(k) - x^(k-1).
-// UPN:  tot[1] = sum_j B_h(D_j x^(k); D_j y^(k)).
+// UPN:  tot[1] = sum_j B_h(D_j x^(k); D_j y^(k)) (from the extrapolation kernel).
 __device__ __forceinline__ void ctrl_after_grad(DevState *st, const double *tot) {
   st->g_evals++;
   st->need_grad = 0;
@@ -176,6 +176,7 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
     st_swap(st->vN[RN_X], st->vN[RN_T]);
     st_swap(st->vM[RM_R], st->vM[RM_RT]);
     st_swap(st->vM[RM_RS], st->vM[RM_RTS]);
+    st_swap(st->w, st->wt);
     const int tr = st->trial;
     st->trial = 0;
     st->need_grad = 1;
@@ -223,6 +224,7 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
   st_swap(st->vN[RN_X], st->vN[RN_T]);
   st_swap(st->vM[RM_R], st->vM[RM_RT]);
   st_swap(st->vM[RM_RS], st->vM[RM_RTS]);
+  if (st->solver != SOLVER_UPN) st_swap(st->w, st->wt);
   const int tr = st->trial;
   st->trial = 0;
   st->need_grad = 1;

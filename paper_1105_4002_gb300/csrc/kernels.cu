@@ -210,7 +210,6 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
   const float *r = rin;
   const float *x = xin;
   float *g = gout;
-  const float *q = nullptr;   // UPN: x^(k) for the Bregman sum at y^(k)
   const float *xo = nullptr;  // GPBB: x^(k-1)
   const float *go = nullptr;  // GPBB: g^(k-1)
   int kind = SOLVER_NONE;
@@ -225,7 +224,6 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
       x = st->vN[RN_Y];
       r = BF ? st->vM[RM_RYS] : st->vM[RM_RY];
       g = st->vN[RN_G];
-      if (MODE == BWD_SOLVER) q = st->vN[RN_X];
     } else {
       x = st->vN[RN_X];
       r = BF ? st->vM[RM_RS] : st->vM[RM_R];
@@ -252,6 +250,23 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     if (valid) {
       beg = __ldg(A.col_ptr + j);
       end = __ldg(A.col_ptr + j + 1);
+    }
+    int ix = 0, iy = 0, iz = 0;
+    if (MODE != BWD_ADJ) voxel_of(A, valid ? j : 0, ix, iy, iz);
+    // solver mode: this lane's term of [grad TV_tau]_j from the Huber weight
+    // planes (lane 0: -(w_0 + w_1 + w_2) at j; lanes 1..3: w_e at j - e),
+    // loaded ahead of the projection loop
+    float c = 0.f;
+    if (MODE == BWD_SOLVER && valid && lane < 4) {
+      const float *__restrict__ W = st->w;
+      if (lane == 0)
+        c = -__ldg(W + 3 * A.N + j);
+      else if (lane == 1)
+        c = ix > 0 ? __ldg(W + j - 1) : 0.f;
+      else if (lane == 2)
+        c = iy > 0 ? __ldg(W + A.N + j - n) : 0.f;
+      else
+        c = iz > 0 ? __ldg(W + 2 * A.N + j - nn) : 0.f;
     }
     float s = 0.f;
     for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kColChunks) {
@@ -290,11 +305,9 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
       if (valid && lane == 0) g[j] = s;
       continue;
     }
-    int ix, iy, iz;
-    voxel_of(A, j, ix, iy, iz);
     Huber hw;
-    float c = 0.f;
-    if (valid && lane < 4) {
+    hw.h = 0.f;
+    if (MODE != BWD_SOLVER && valid && lane < 4) {
       huber_at(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, hw);
       c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2])
                     : (lane == 1 ? hw.w[0] : (lane == 2 ? hw.w[1] : hw.w[2]));
@@ -308,20 +321,11 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     if (valid && lane == 0) {
       const float gj = __fmaf_rn(alpha, c, s);
       g[j] = gj;
-      ff_add(a0, hw.h);
+      if (MODE != BWD_SOLVER) ff_add(a0, hw.h);
       if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
         const float sj = __fsub_rn(x[j], xo[j]);
         ff_add_prod(a1, sj, __fsub_rn(gj, go[j]));
         ff_add_prod(a2, sj, sj);
-      }
-      if (MODE == BWD_SOLVER && kind == SOLVER_UPN) {
-        float zb[3], dl[3];
-        diff3(q, ix, iy, iz, n, zb);
-        const float d0 = __fsub_rn(q[j], x[j]);
-        dl[0] = ix + 1 < n ? __fsub_rn(__fsub_rn(q[j + 1], x[j + 1]), d0) : 0.f;
-        dl[1] = iy + 1 < n ? __fsub_rn(__fsub_rn(q[j + n], x[j + n]), d0) : 0.f;
-        dl[2] = iz + 1 < n ? __fsub_rn(__fsub_rn(q[j + nn], x[j + nn]), d0) : 0.f;
-        ff_add(a1, huber_bregman(hw.z, hw.nrm, zb, dl, tau));
       }
     }
   }
@@ -348,6 +352,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     } else if (MODE == BWD_INIT) {
       ctrl_init(st, tot);
     } else {
+      if (kind == SOLVER_UPN) tot[1] = st->r_yf[2];  // TV Bregman sum from the extrapolation
       st->r_bwd[0] = tot[0];
       st->r_bwd[1] = tot[1];
       st->r_bwd[2] = tot[2];
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
 // recomputed with the same expression, so the TV Bregman sum sees exactly the
 // stored values.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK, 5)
+__global__ void __launch_bounds__(TVR_BLOCK, 4)
     k_step(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
   pdl_enter();
   if (st->done) return;
@@ -379,6 +384,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, 5)
   const float tau = (float)st->tau;
   const int n = A.n;
   const int64_t nn = (int64_t)n * n;
+  const int64_t N = A.N;
+  float *__restrict__ wt = upn ? nullptr : st->wt;
   FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero();
   const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
   for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < A.N; j += stride) {
@@ -410,7 +417,16 @@ __global__ void __launch_bounds__(TVR_BLOCK, 5)
         z[e] = zb[e] = dl[e] = 0.f;
       }
     }
-    ff_add(a2, huber_bregman(z, norm3(z), zb, dl, tau));
+    const float nb = norm3(zb);
+    ff_add(a2, huber_bregman_n(z, norm3(z), zb, nb, dl, tau));
+    if (wt) {  // Huber weights at xbar for the gradient that follows acceptance
+      float w[3];
+      huber_weights(zb, nb, tau, w);
+      wt[j] = w[0];
+      wt[N + j] = w[1];
+      wt[2 * N + j] = w[2];
+      wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
+    }
   }
   FF acc[4] = {a0, a1, a2, a3};
   double tot[4];
@@ -424,9 +440,13 @@ __global__ void __launch_bounds__(TVR_BLOCK, 5)
 // UPN extrapolation (Alg. 3): y = x+ + beta (x+ - x) and, by linearity of A,
 //   u  = A(x+ - x) = A(x+ - y_prev) + beta_prev u_prev,
 //   A y - b = (A x+ - b) + beta u,
-// so the residual at y needs no projection.  Reductions: ||x+ - x||^2, ||u||^2.
+// so the residual at y needs no projection.  The kernel also writes the Huber
+// weights of D y (the TV part of the gradient at y) and sums the TV Bregman
+// term sum_j B_h(D_j x+; D_j y) of the mu-estimate, recomputing y at the
+// forward neighbours with the same expression.  Reductions: ||x+ - x||^2,
+// ||u||^2, sum_j B_h.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK)
+__global__ void __launch_bounds__(TVR_BLOCK, 4)
     k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
   pdl_enter();
   if (st->done || !st->need_grad) return;
@@ -440,15 +460,47 @@ __global__ void __launch_bounds__(TVR_BLOCK)
   const float *__restrict__ AD = st->vM[RM_AD];
   float *__restrict__ U = st->vM[RM_U];
   float *__restrict__ RY = st->vM[RM_RY];
-  FF a0 = ff_zero(), a1 = ff_zero();
+  float *__restrict__ W = st->w;
+  const float tau = (float)st->tau;
+  const int n = A.n;
+  const int64_t N = A.N;
+  const int64_t nn = (int64_t)n * n;
+  FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
   const int64_t lim = A.N > A.m ? A.N : A.m;
   const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
   for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < lim; i += stride) {
     if (i < A.N) {
       const float xn = X[i];
       const float dx = __fsub_rn(xn, T[i]);
-      Y[i] = __fmaf_rn(beta, dx, xn);
+      const float yj = __fmaf_rn(beta, dx, xn);
+      Y[i] = yj;
       ff_add_prod(a0, dx, dx);
+      int ix, iy, iz;
+      voxel_of(A, i, ix, iy, iz);
+      const int64_t off[3] = {1, n, nn};
+      const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
+      const float dq0 = __fsub_rn(xn, yj);
+      float z[3], zq[3], dl[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        if (in[e]) {
+          const float xk = X[i + off[e]];
+          const float yk = __fmaf_rn(beta, __fsub_rn(xk, T[i + off[e]]), xk);
+          z[e] = __fsub_rn(yk, yj);
+          zq[e] = __fsub_rn(xk, xn);
+          dl[e] = __fsub_rn(__fsub_rn(xk, yk), dq0);
+        } else {
+          z[e] = zq[e] = dl[e] = 0.f;
+        }
+      }
+      const float nz = norm3(z);
+      float w[3];
+      huber_weights(z, nz, tau, w);
+      W[i] = w[0];
+      W[N + i] = w[1];
+      W[2 * N + i] = w[2];
+      W[3 * N + i] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
+      ff_add(a2, huber_bregman(z, nz, zq, dl, tau));
     }
     if (i < A.m) {
       const float u = __fmaf_rn(bp, U[i], AD[i]);
@@ -459,11 +511,12 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       ff_add_prod(a1, u, u);
     }
   }
-  FF acc[2] = {a0, a1};
-  double tot[2];
-  if (grid_reduce<2>(acc, slot, tot) && threadIdx.x == 0) {
+  FF acc[3] = {a0, a1, a2};
+  double tot[3];
+  if (grid_reduce<3>(acc, slot, tot) && threadIdx.x == 0) {
     st->r_yf[0] = tot[0];
     st->r_yf[1] = tot[1];
+    st->r_yf[2] = tot[2];
   }
 }
 

@@ -27,6 +27,8 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
   for (int k = 0; k < nm; ++k)
     if (int rc = ensure_vec(&sys->vM[k], sys->m)) return rc;
   if (!sys->t2) TVR_CUDA(cudaMalloc(&sys->t2, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));
+  for (auto &w : sys->wplanes)
+    if (!w) TVR_CUDA(cudaMalloc(&w, sizeof(float) * 4 * (sys->N > 0 ? sys->N : 1)));
   if (!sys->st) TVR_CUDA(cudaMalloc(&sys->st, sizeof(DevState)));
   if (!sys->pinned_flag) TVR_CUDA(cudaMallocHost(&sys->pinned_flag, 64));
   if (!sys->cap_stream) TVR_CUDA(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking));
@@ -204,6 +206,8 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
   for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
   h.t2 = sys->t2;
+  h.w = sys->wplanes[0];
+  h.wt = sys->wplanes[1];
   h.hist = j.hist_n > 0 ? sys->hist_dev : nullptr;
   h.prof_flags = sys->prof_flags_dev;
   h.hist_cap = (int)j.hist_n;

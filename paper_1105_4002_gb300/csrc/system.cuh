@@ -40,6 +40,7 @@ struct tvr_system {
   float *vN[RN_COUNT] = {};
   float *vM[RM_COUNT] = {};
   float2 *t2 = nullptr;
+  float *wplanes[2] = {nullptr, nullptr};  // Huber weight planes (4 N floats each)
   double *hist_dev = nullptr;
   int hist_cap = 0;
   int *pinned_flag = nullptr;

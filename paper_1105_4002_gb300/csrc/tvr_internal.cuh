@@ -193,9 +193,8 @@ __device__ __forceinline__ void huber_at(const float *__restrict__ x, int ix, in
 // in a form without cancellation when both points lie in the same zone:
 //   quadratic zone: |dlt|^2 / (2 tau);
 //   linear zone:    |z x dlt|^2 / (|z| (|zb||z| + z.zb))  when z.zb > 0.
-__device__ __forceinline__ float huber_bregman(const float z[3], float nz, const float zb[3],
-                                               const float dlt[3], float tau) {
-  const float nb = norm3(zb);
+__device__ __forceinline__ float huber_bregman_n(const float z[3], float nz, const float zb[3],
+                                                 float nb, const float dlt[3], float tau) {
   if (nz < tau && nb < tau) {
     const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dlt[0], dlt[0]), __fmul_rn(dlt[1], dlt[1])),
                                __fmul_rn(dlt[2], dlt[2]));
@@ -216,6 +215,18 @@ __device__ __forceinline__ float huber_bregman(const float z[3], float nz, const
                              den);
   const float b = __fsub_rn(__fsub_rn(huber_h(nb, tau), huber_h(nz, tau)), wd);
   return fmaxf(b, 0.f);
+}
+
+__device__ __forceinline__ float huber_bregman(const float z[3], float nz, const float zb[3],
+                                               const float dlt[3], float tau) {
+  return huber_bregman_n(z, nz, zb, norm3(zb), dlt, tau);
+}
+
+// Huber weights of a difference vector z with |z| = nrm: w_e = z_e / max(tau, |z|).
+__device__ __forceinline__ void huber_weights(const float z[3], float nrm, float tau, float w[3]) {
+  const float den = fmaxf(tau, nrm);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) w[e] = __fdiv_rn(z[e], den);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,6 +265,13 @@ struct DevState {
   float *vN[RN_COUNT];
   float *vM[RM_COUNT];
   float2 *t2;  // trial point and step interleaved: (xbar_j, xbar_j - base_j)
+  // Huber weights w_e(D_j v) of the point v where the next gradient is taken,
+  // as 4 planes of N floats: w_0, w_1, w_2 and (w_0 + w_1) + w_2.  `w` holds
+  // them for the gradient point (written by the extrapolation kernel in UPN),
+  // `wt` for the trial point of GP / GPBB (written by the step kernel; the
+  // two swap on acceptance).  The back projection then reads the TV gradient
+  // instead of re-evaluating the stencil.
+  float *w, *wt;
   // history (device buffer of hist_cap records)
   double *hist;
   int hist_cap, hist_used;
