@@ -77,25 +77,70 @@ struct RedSlot {
   double *out;         // [TVR_RMAX] final sums (FP64)
 };
 
-// Block-wide reduction of R pairs; the result is valid in thread 0.
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int mask) {
+  FF b;
+  b.hi = __shfl_xor_sync(0xffffffffu, a.hi, mask);
+  b.lo = __shfl_xor_sync(0xffffffffu, a.lo, mask);
+  return b;
+}
+
+// Warp-wide reduce-scatter of R <= 4 pairs: after it, the lanes of each group
+// of 32 / P (P = R rounded up to a power of two) hold the warp total of value
+// k = lane / (32 / P).  Each exchange step halves the values a lane carries, so
+// R values cost 2 + 1 + 3 merges (R = 3, 4) instead of 5 R.  ff_merge is
+// commutative, so both partners of an exchange hold the same result.
+template <int R>
+__device__ __forceinline__ FF warp_reduce_scatter(const FF (&a)[R]) {
+  static_assert(R >= 1 && R <= 4, "R");
+  const int lane = threadIdx.x & 31;
+  if constexpr (R == 1) {
+    FF v = a[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = ff_merge(v, ff_shfl_xor(v, o));
+    return v;
+  } else if constexpr (R == 2) {
+    const bool h16 = lane & 16;
+    FF keep = h16 ? a[1] : a[0];
+    keep = ff_merge(keep, ff_shfl_xor(h16 ? a[0] : a[1], 16));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) keep = ff_merge(keep, ff_shfl_xor(keep, o));
+    return keep;
+  } else {
+    const FF a3 = R == 4 ? a[R - 1] : ff_zero();
+    const bool h16 = lane & 16, h8 = lane & 8;
+    FF k0 = h16 ? a[2] : a[0], k1 = h16 ? a3 : a[1];
+    const FF s0 = h16 ? a[0] : a[2], s1 = h16 ? a[1] : a3;
+    k0 = ff_merge(k0, ff_shfl_xor(s0, 16));
+    k1 = ff_merge(k1, ff_shfl_xor(s1, 16));
+    FF keep = h8 ? k1 : k0;
+    keep = ff_merge(keep, ff_shfl_xor(h8 ? k0 : k1, 8));
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) keep = ff_merge(keep, ff_shfl_xor(keep, o));
+    return keep;
+  }
+}
+
+// Block-wide reduction of R pairs; the result is valid in every lane of warp 0.
+// Warps reduce-scatter, then warp 0 holds value k of warp w in lane k W + w
+// (W warps) and reduces within groups of W lanes.
 template <int R>
 __device__ __forceinline__ void block_reduce(FF (&a)[R]) {
-  __shared__ FF sh[TVR_BLOCK / 32][R];
+  constexpr int P = R == 1 ? 1 : (R == 2 ? 2 : 4);
+  constexpr int W = TVR_BLOCK / 32;
+  static_assert(P * W <= 32 && (W & (W - 1)) == 0, "block shape");
+  __shared__ FF sh[P][W];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < R; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[k] = ff_merge(a[k], ff_shfl_down(a[k], o));
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < R; ++k) sh[warp][k] = a[k];
+  const FF v = warp_reduce_scatter<R>(a);
+  if ((lane & (32 / P - 1)) == 0) sh[lane / (32 / P)][warp] = v;
   __syncthreads();
   if (warp == 0) {
+    FF u = lane < P * W ? sh[lane / W][lane % W] : ff_zero();
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) u = ff_merge(u, ff_shfl_xor(u, o));
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      a[k] = lane < TVR_BLOCK / 32 ? sh[lane][k] : ff_zero();
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a[k] = ff_merge(a[k], ff_shfl_down(a[k], o));
+      a[k].hi = __shfl_sync(0xffffffffu, u.hi, k * W);
+      a[k].lo = __shfl_sync(0xffffffffu, u.lo, k * W);
     }
   }
   __syncthreads();
