@@ -483,6 +483,7 @@ def main():
     evals = 0
     passes = 0
     launches = 0
+    trials_gpbb = trials_upn = 0
     t_gpbb, t_upn, it_gpbb, it_upn = [], [], [], []
     for _ in range(args.steps):
         s0 = time.perf_counter()
@@ -496,8 +497,11 @@ def main():
         it_upn.append(r2.iters)
         evals += r1.g_evals + r2.g_evals
         passes += r1.passes + r2.passes
-        # init (2) + per pass (3 GPBB / 4 UPN) + final phi (2)
-        launches += 2 + 3 * r1.passes + 2 + 2 + 4 * r2.passes + 2
+        trials_gpbb += r1.f_evals - 1
+        trials_upn += r2.f_evals - 1
+        # init (2) + per pass (2 GPBB / 3 UPN: the step is fused into the trial forward)
+        # + final phi (2)
+        launches += 2 + 2 * r1.passes + 2 + 2 + 3 * r2.passes + 2
     ev1.record()
     torch.cuda.synchronize()
     if dist:
@@ -578,15 +582,22 @@ def main():
     # or bfloat16 plus a float32 scale per row and a scaled residual)
     vb = 4 if args.storage == "fp32" else 2
     extra_m = 0 if args.storage == "fp32" else 8
-    bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 3 * 4 * N
-    bytes_fwd = (4 + vb) * nnz + 8 * (m + 1) + 2 * 4 * N + 3 * 4 * m + extra_m * m
+    # solver back projection: A^T (values + indices), column pointers, r gather,
+    # the four Huber weight planes, x read and g and (p, g) written
+    bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
+    # trial forward with the fused step: A (values + indices), row pointers, the
+    # (p, g) pairs, b, r and A d (UPN) rows, xbar written, and for GPBB trials
+    # the four Huber weight planes (weighted by the share of GPBB trials)
+    w_share = trials_gpbb / max(trials_gpbb + trials_upn, 1)
+    bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 3 * 4 * m + extra_m * m
+                 + w_share * 16 * N)
     peak, peak_kind = measured_peak_gbs()
     roof = None
     nf, msf = prof["forward"]
     if nf:
         avg_s = msf / nf / 1e3
         ach = bytes_fwd / avg_s / 1e9
-        bk = {k: 1e3 * v[1] / max(v[0], 1) for k, v in breakdown.items()}
+        bk = {k: 1e3 * v[1] / v[0] for k, v in breakdown.items() if v[0]}
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": captured_traffic("fwd_csr_trial", args.storage), "kernel": "fwd_csr_trial",
                 "launches": nf, "avg_us": 1e6 * avg_s, "algorithmic_bytes_per_launch": bytes_fwd,
@@ -597,7 +608,8 @@ def main():
                 "breakdown_frac": {"forward": bytes_fwd / (bk["forward"] / 1e6) / 1e9 / peak,
                                    "backward": bytes_bwd / (bk["backward"] / 1e6) / 1e9 / peak},
                 "breakdown_note": "per-launch means of one extra step with every kernel timed "
-                                  "(event nodes around each kernel slow the small ones)"}
+                                  "(event nodes around each kernel slow the small ones); the "
+                                  "projected step runs inside the trial forward kernel"}
     pf, pb = phi_prof["forward"], phi_prof["backward"]
     plain_f = (4 + vb) * nnz + 8 * (m + 1) + 4 * N + 8 * m + extra_m * m
     plain_b = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 8 * N

@@ -312,11 +312,16 @@ TVR_API int tvr_solve_sweep(const tvr_system *sys, int32_t method, const float *
  * to time (0 = off, 1 = forward only, 15 = all); bits 8-15 give a sampling
  * stride for solves replayed as pass graphs (time every stride-th pass of a
  * batch; 0 or 1 = every pass).  While enabled, the library records a CUDA
- * event pair on the launch stream around every forward (CSR) and back (CSC +
- * TV) projection kernel launched outside a CUDA graph.  tvr_profile_read
- * synchronises those events and returns, per kernel kind (0 = forward,
- * 1 = back projection), the number of timed launches and their total time in
- * milliseconds (host outputs), then resets the counters.
+ * event pair on the launch stream around every selected kernel (event nodes
+ * inside a pass graph, so graph replays are timed too) and counts only the
+ * launches that did work.  Kinds: 0 = forward projection (in a solve, the
+ * trial kernel, which also carries the projected step over the voxels),
+ * 1 = back projection (CSC + TV), 2 = step (no separate launches: fused into
+ * kind 0, kept for the array layout), 3 = UPN extrapolation.
+ * tvr_profile_read synchronises the events and returns, per kind, the number
+ * of timed launches and their total time in milliseconds (host outputs), then
+ * resets the counters.  Event nodes around a kernel break the programmatic
+ * launch overlap at that point, so timed passes run slightly slower.
  */
 TVR_API int tvr_profile_enable(tvr_system *sys, int32_t enable);
 TVR_API int tvr_profile_read(tvr_system *sys, int64_t counts[4], double total_ms[4]);

@@ -95,7 +95,7 @@ int tvr_system_free(tvr_system *sys) {
   sweep_free(sys->sweep);
   if (sys->stage_sweepX) cudaFree(sys->stage_sweepX);
   void *ptrs[] = {sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
-                  sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev, sys->t2,
+                  sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev, sys->pg,
                   sys->wplanes[0], sys->wplanes[1]};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -1,10 +1,12 @@
 // Hot-path kernels of the TV-CT gradient methods (sm_103a).
 //
-//   k_forward   r = A x - b (CSR, row-parallel), 1/2||r||^2; trial mode also A(x - p)
+//   k_forward   r = A x - b (CSR, row-parallel), 1/2||r||^2; trial mode gathers (p, g),
+//               forms xbar = P_Q(p - s g) per entry for A xbar and A(xbar - p), and
+//               fuses the projected step over the voxels (g^T d, ||d||^2, sum_j B_h,
+//               the Huber weights at xbar) with the acceptance test
 //   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free) fused with
 //               the TV_tau stencil and its value; solver modes add the BB dots
 //               (GPBB) or the TV Bregman sum of the mu-estimate (UPN)
-//   k_step      xbar = P_Q(p - s g) with g^T d, ||d||^2, sum_j B_h (step + projection)
 //   k_yform     UPN extrapolation y = x+ + beta (x+ - x) and its residual A y - b
 //   k_tv_value  TV_tau(x) alone (phi without a gradient)
 //   k_project   P_Q in place; k_gmap gradient-map norm
@@ -67,6 +69,41 @@ __device__ __forceinline__ float4 load4(const float *__restrict__ v32,
   return __ldg(reinterpret_cast<const float4 *>(v32 + e));
 }
 
+__device__ __forceinline__ float xbar_of(float p, float g, float s) {
+  return proj(__fsub_rn(p, __fmul_rn(s, g)));
+}
+
+// Per-voxel part of the step: d = xbar_j - p_j, the terms of g^T d, ||d||^2,
+// the GPBB ||x - P(x - theta g)||^2 and the TV Bregman sum, and the Huber
+// weights at xbar.  pk / xk: p and xbar at the forward neighbours (in[e]).
+__device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const float pk[3],
+                                            const float xk[3], const bool in[3], float s2,
+                                            bool want_g2, float tau, FF &a0, FF &a1, FF &a2,
+                                            FF &a3, float w[3]) {
+  const float d = __fsub_rn(xb, pj);
+  ff_add_prod(a0, gj, d);
+  ff_add_prod(a1, d, d);
+  if (want_g2) {
+    const float e = __fsub_rn(pj, proj(__fsub_rn(pj, __fmul_rn(s2, gj))));
+    ff_add_prod(a3, e, e);
+  }
+  float z[3], zb[3], dl[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (in[e]) {
+      z[e] = __fsub_rn(pk[e], pj);
+      zb[e] = __fsub_rn(xk[e], xb);
+      dl[e] = __fsub_rn(__fsub_rn(xk[e], pk[e]), d);
+    } else {
+      z[e] = zb[e] = dl[e] = 0.f;
+    }
+  }
+  const float nb = norm3(zb);
+  ff_add(a2, huber_bregman_n(z, norm3(z), zb, nb, dl, tau));
+  huber_weights(zb, nb, tau, w);
+  return d;
+}
+
 enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3 };
 enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP = 4 };
 
@@ -81,7 +118,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
               float *__restrict__ rsout = nullptr) {
   pdl_enter();
   const float *x = xin;
-  const float2 *xd = nullptr;  // trial mode: (xbar, xbar - base) per voxel
+  const float2 *pg = nullptr;  // trial mode: (p_j, g_j) per voxel
+  float s = 0.f;               // trial mode: step size
   float *r = rout;
   float *rs = rsout;           // BF16 storage: r times the row scale
   float *ad = nullptr;
@@ -96,7 +134,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->prof_flags[prof_slot] = 1;
     const bool upn = st->solver == SOLVER_UPN;
     b = st->b;
-    xd = st->t2;
+    pg = st->pg;
+    s = (float)st->step;
     r = st->vM[RM_RT];
     rs = st->vM[RM_RTS];
     ad = upn ? st->vM[RM_AD] : nullptr;
@@ -138,16 +177,19 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
       for (int u = 0; u < kRowChunks; ++u) {
         if (e0 + (int64_t)u * 4 * G >= end) break;
         if (MODE == FWD_TRIAL) {
-          const float2 t0 = __ldg(xd + c4[u].x), t1 = __ldg(xd + c4[u].y);
-          const float2 t2 = __ldg(xd + c4[u].z), t3 = __ldg(xd + c4[u].w);
-          sx = __fmaf_rn(v4[u].x, t0.x, sx);
-          sd = __fmaf_rn(v4[u].x, t0.y, sd);
-          sx = __fmaf_rn(v4[u].y, t1.x, sx);
-          sd = __fmaf_rn(v4[u].y, t1.y, sd);
-          sx = __fmaf_rn(v4[u].z, t2.x, sx);
-          sd = __fmaf_rn(v4[u].z, t2.y, sd);
-          sx = __fmaf_rn(v4[u].w, t3.x, sx);
-          sd = __fmaf_rn(v4[u].w, t3.y, sd);
+          // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
+          const float2 q0 = __ldg(pg + c4[u].x), q1 = __ldg(pg + c4[u].y);
+          const float2 q2 = __ldg(pg + c4[u].z), q3 = __ldg(pg + c4[u].w);
+          const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
+          const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
+          sx = __fmaf_rn(v4[u].x, b0, sx);
+          sd = __fmaf_rn(v4[u].x, __fsub_rn(b0, q0.x), sd);
+          sx = __fmaf_rn(v4[u].y, b1, sx);
+          sd = __fmaf_rn(v4[u].y, __fsub_rn(b1, q1.x), sd);
+          sx = __fmaf_rn(v4[u].z, b2, sx);
+          sd = __fmaf_rn(v4[u].z, __fsub_rn(b2, q2.x), sd);
+          sx = __fmaf_rn(v4[u].w, b3, sx);
+          sd = __fmaf_rn(v4[u].w, __fsub_rn(b3, q3.x), sd);
         } else {
           const float x0 = __ldg(x + c4[u].x), x1 = __ldg(x + c4[u].y);
           const float x2 = __ldg(x + c4[u].z), x3 = __ldg(x + c4[u].w);
@@ -182,15 +224,62 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     }
   }
   if (MODE == FWD_Y) return;
-  FF acc[2] = {a0, a1};
-  double tot[2];
-  if (grid_reduce<2>(acc, slot, tot) && threadIdx.x == 0) {
-    if (MODE == FWD_INIT) st->r_init[0] = tot[0];
-    if (MODE == FWD_TRIAL) {
-      st->r_fwd[0] = tot[0];
-      st->r_fwd[1] = tot[1];
-      ctrl_trial(st, tot);
+  if (MODE != FWD_TRIAL) {
+    FF acc[1] = {a0};
+    double tot[1];
+    if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0 && MODE == FWD_INIT)
+      st->r_init[0] = tot[0];
+    return;
+  }
+  // Step phase: xbar = P_Q(p - s g) (eq. gradientmethod; Alg. 1, Alg. 2) over
+  // the voxels, with the reductions of the acceptance tests.  xbar at the
+  // forward neighbours is recomputed with the same expression, so the TV
+  // Bregman sum and the Huber weights (written for GP / GPBB, whose next
+  // gradient is taken at the accepted xbar) see exactly the stored values.
+  FF s0 = ff_zero(), s1 = ff_zero(), s2 = ff_zero(), s3 = ff_zero();
+  {
+    const bool upn = st->solver == SOLVER_UPN;
+    const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
+    const float sg2 = (float)st->step2;
+    const float tau = (float)st->tau;
+    float *__restrict__ t = st->vN[RN_T];
+    float *__restrict__ wt = upn ? nullptr : st->wt;
+    const int n = A.n;
+    const int64_t nn = (int64_t)n * n, N = A.N;
+    const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+    for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < N; j += stride) {
+      const float2 q = pg[j];
+      const float xb = xbar_of(q.x, q.y, s);
+      int ix, iy, iz;
+      voxel_of(A, j, ix, iy, iz);
+      const int64_t off[3] = {1, n, nn};
+      const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
+      float pk[3], xk[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const float2 qk = in[e] ? pg[j + off[e]] : make_float2(0.f, 0.f);
+        pk[e] = qk.x;
+        xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
+      }
+      float w[3];
+      step_voxel(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, w);
+      t[j] = xb;
+      if (wt) {
+        wt[j] = w[0];
+        wt[N + j] = w[1];
+        wt[2 * N + j] = w[2];
+        wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
+      }
     }
+  }
+  FF acc[6] = {a0, a1, s0, s1, s2, s3};
+  double tot[6];
+  if (grid_reduce<6>(acc, slot, tot) && threadIdx.x == 0) {
+    st->r_fwd[0] = tot[0];
+    st->r_fwd[1] = tot[1];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st->r_step[k] = tot[2 + k];
+    ctrl_trial(st, tot);
   }
 }
 
@@ -321,6 +410,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     if (valid && lane == 0) {
       const float gj = __fmaf_rn(alpha, c, s);
       g[j] = gj;
+      if (MODE == BWD_INIT || MODE == BWD_SOLVER) st->pg[j] = make_float2(x[j], gj);
       if (MODE != BWD_SOLVER) ff_add(a0, hw.h);
       if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
         const float sj = __fsub_rn(x[j], xo[j]);
@@ -362,81 +452,6 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
 }
 
 // ---------------------------------------------------------------------------
-// Projected step xbar = P_Q(p - s g) (eq. gradientmethod; Alg. 1, Alg. 2) with
-// the reductions of the acceptance tests.  xbar at the forward neighbours is
-// recomputed with the same expression, so the TV Bregman sum sees exactly the
-// stored values.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TVR_BLOCK, 4)
-    k_step(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
-  pdl_enter();
-  if (st->done) return;
-  if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
-    st->prof_flags[2 * TVR_PROF_PAIRS + prof_slot] = 1;
-  const bool upn = st->solver == SOLVER_UPN;
-  const float *__restrict__ p = upn ? st->vN[RN_Y] : st->vN[RN_X];
-  const float *__restrict__ g = st->vN[RN_G];
-  float *__restrict__ t = st->vN[RN_T];
-  float2 *__restrict__ t2 = st->t2;
-  const float s = (float)st->step;
-  const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
-  const float s2 = (float)st->step2;
-  const float tau = (float)st->tau;
-  const int n = A.n;
-  const int64_t nn = (int64_t)n * n;
-  const int64_t N = A.N;
-  float *__restrict__ wt = upn ? nullptr : st->wt;
-  FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero(), a3 = ff_zero();
-  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
-  for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < A.N; j += stride) {
-    const float pj = p[j], gj = g[j];
-    const float xb = proj(__fsub_rn(pj, __fmul_rn(s, gj)));
-    t[j] = xb;
-    const float d = __fsub_rn(xb, pj);
-    t2[j] = make_float2(xb, d);
-    ff_add_prod(a0, gj, d);
-    ff_add_prod(a1, d, d);
-    if (want_g2) {
-      const float e = __fsub_rn(pj, proj(__fsub_rn(pj, __fmul_rn(s2, gj))));
-      ff_add_prod(a3, e, e);
-    }
-    int ix, iy, iz;
-    voxel_of(A, j, ix, iy, iz);
-    float z[3], zb[3], dl[3];
-    const int64_t off[3] = {1, n, nn};
-    const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      if (in[e]) {
-        const float pk = p[j + off[e]], gk = g[j + off[e]];
-        const float xk = proj(__fsub_rn(pk, __fmul_rn(s, gk)));
-        z[e] = __fsub_rn(pk, pj);
-        zb[e] = __fsub_rn(xk, xb);
-        dl[e] = __fsub_rn(__fsub_rn(xk, pk), d);
-      } else {
-        z[e] = zb[e] = dl[e] = 0.f;
-      }
-    }
-    const float nb = norm3(zb);
-    ff_add(a2, huber_bregman_n(z, norm3(z), zb, nb, dl, tau));
-    if (wt) {  // Huber weights at xbar for the gradient that follows acceptance
-      float w[3];
-      huber_weights(zb, nb, tau, w);
-      wt[j] = w[0];
-      wt[N + j] = w[1];
-      wt[2 * N + j] = w[2];
-      wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
-    }
-  }
-  FF acc[4] = {a0, a1, a2, a3};
-  double tot[4];
-  if (grid_reduce<4>(acc, slot, tot) && threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) st->r_step[k] = tot[k];
-  }
-}
-
-// ---------------------------------------------------------------------------
 // UPN extrapolation (Alg. 3): y = x+ + beta (x+ - x) and, by linearity of A,
 //   u  = A(x+ - x) = A(x+ - y_prev) + beta_prev u_prev,
 //   A y - b = (A x+ - b) + beta u,
@@ -446,8 +461,34 @@ __global__ void __launch_bounds__(TVR_BLOCK, 4)
 // forward neighbours with the same expression.  Reductions: ||x+ - x||^2,
 // ||u||^2, sum_j B_h.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float y_of(float xn, float xo, float beta) {
+  return __fmaf_rn(beta, __fsub_rn(xn, xo), xn);
+}
+
+// Per-voxel part: Huber weights of D y and the Bregman term at voxel j.
+// xk / yk: x+ and y at the forward neighbours (in[e]).
+__device__ __forceinline__ void yform_voxel(float xn, float yj, const float xk[3],
+                                            const float yk[3], const bool in[3], float tau,
+                                            FF &a2, float w[3]) {
+  const float dq0 = __fsub_rn(xn, yj);
+  float z[3], zq[3], dl[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (in[e]) {
+      z[e] = __fsub_rn(yk[e], yj);
+      zq[e] = __fsub_rn(xk[e], xn);
+      dl[e] = __fsub_rn(__fsub_rn(xk[e], yk[e]), dq0);
+    } else {
+      z[e] = zq[e] = dl[e] = 0.f;
+    }
+  }
+  const float nz = norm3(z);
+  huber_weights(z, nz, tau, w);
+  ff_add(a2, huber_bregman(z, nz, zq, dl, tau));
+}
+
 __global__ void __launch_bounds__(TVR_BLOCK, 4)
-    k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot = -1) {
+    k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot) {
   pdl_enter();
   if (st->done || !st->need_grad) return;
   if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
@@ -460,16 +501,16 @@ __global__ void __launch_bounds__(TVR_BLOCK, 4)
   const float *__restrict__ AD = st->vM[RM_AD];
   float *__restrict__ U = st->vM[RM_U];
   float *__restrict__ RY = st->vM[RM_RY];
+  float *__restrict__ RYS = A.bf16 ? st->vM[RM_RYS] : nullptr;
   float *__restrict__ W = st->w;
   const float tau = (float)st->tau;
   const int n = A.n;
-  const int64_t N = A.N;
+  const int64_t N = A.N, m = A.m;
   const int64_t nn = (int64_t)n * n;
   FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
-  const int64_t lim = A.N > A.m ? A.N : A.m;
+  const int64_t tid = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
-  for (int64_t i = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; i < lim; i += stride) {
-    if (i < A.N) {
+    for (int64_t i = tid; i < N; i += stride) {
       const float xn = X[i];
       const float dx = __fsub_rn(xn, T[i]);
       const float yj = __fmaf_rn(beta, dx, xn);
@@ -479,37 +520,27 @@ __global__ void __launch_bounds__(TVR_BLOCK, 4)
       voxel_of(A, i, ix, iy, iz);
       const int64_t off[3] = {1, n, nn};
       const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
-      const float dq0 = __fsub_rn(xn, yj);
-      float z[3], zq[3], dl[3];
+      float xk[3], yk[3];
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
-        if (in[e]) {
-          const float xk = X[i + off[e]];
-          const float yk = __fmaf_rn(beta, __fsub_rn(xk, T[i + off[e]]), xk);
-          z[e] = __fsub_rn(yk, yj);
-          zq[e] = __fsub_rn(xk, xn);
-          dl[e] = __fsub_rn(__fsub_rn(xk, yk), dq0);
-        } else {
-          z[e] = zq[e] = dl[e] = 0.f;
-        }
+        xk[e] = in[e] ? X[i + off[e]] : 0.f;
+        yk[e] = in[e] ? y_of(xk[e], T[i + off[e]], beta) : 0.f;
       }
-      const float nz = norm3(z);
       float w[3];
-      huber_weights(z, nz, tau, w);
+      yform_voxel(xn, yj, xk, yk, in, tau, a2, w);
       W[i] = w[0];
       W[N + i] = w[1];
       W[2 * N + i] = w[2];
       W[3 * N + i] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
-      ff_add(a2, huber_bregman(z, nz, zq, dl, tau));
-    }
-    if (i < A.m) {
-      const float u = __fmaf_rn(bp, U[i], AD[i]);
-      U[i] = u;
-      const float ry = __fmaf_rn(beta, u, R[i]);
-      RY[i] = ry;
-      if (A.bf16) st->vM[RM_RYS][i] = __fmul_rn(A.rscale[i], ry);
-      ff_add_prod(a1, u, u);
-    }
+  }
+  // residual at y by linearity (rows)
+  for (int64_t i = tid; i < m; i += stride) {
+    const float u = __fmaf_rn(bp, U[i], AD[i]);
+    U[i] = u;
+    const float ry = __fmaf_rn(beta, u, R[i]);
+    RY[i] = ry;
+    if (RYS) RYS[i] = __fmul_rn(A.rscale[i], ry);
+    ff_add_prod(a1, u, u);
   }
   FF acc[3] = {a0, a1, a2};
   double tot[3];
@@ -592,7 +623,7 @@ void kernel_grids(Workspace &ws, int device) {
       occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device);
   ws.grid_bwd =
       occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device);
-  ws.grid_elem = occupancy_grid((const void *)k_step, TVR_BLOCK, device);
+  ws.grid_elem = occupancy_grid((const void *)k_yform, TVR_BLOCK, device);
 }
 
 // Launch with programmatic stream serialization (the kernel calls pdl_enter
@@ -694,9 +725,6 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
   launch_pdl(bwd_kernel<BWD_SOLVER>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
              ws.bwd, nullptr, nullptr, st, slot(1), nullptr, nullptr);
   mark(1, 1);
-  mark(2, 0);
-  launch_pdl(k_step, elem_grid(A.N, ws.grid_elem), s, A, ws.step, st, slot(2));
-  mark(2, 1);
   mark(0, 0);
   launch_pdl(fwd_kernel<FWD_TRIAL>(A), ws.grid_fwd, s, A, nullptr, nullptr, nullptr, ws.fwd, st,
              slot(0), nullptr);

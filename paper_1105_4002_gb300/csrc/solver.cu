@@ -26,7 +26,7 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
   const int nm = sys->A.storage == TVR_STORAGE_BF16_ROWSCALE ? RM_COUNT : RM_RS;
   for (int k = 0; k < nm; ++k)
     if (int rc = ensure_vec(&sys->vM[k], sys->m)) return rc;
-  if (!sys->t2) TVR_CUDA(cudaMalloc(&sys->t2, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));
+  if (!sys->pg) TVR_CUDA(cudaMalloc(&sys->pg, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));
   for (auto &w : sys->wplanes)
     if (!w) TVR_CUDA(cudaMalloc(&w, sizeof(float) * 4 * (sys->N > 0 ? sys->N : 1)));
   if (!sys->st) TVR_CUDA(cudaMalloc(&sys->st, sizeof(DevState)));
@@ -41,6 +41,10 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
   }
   return TVR_OK;
 }
+
+// Kernel kinds a solver pass launches: forward (with the fused step), back
+// projection, and the extrapolation in UPN.
+bool pass_kind(int k, int solver) { return k == 0 || k == 1 || (k == 3 && solver == SOLVER_UPN); }
 
 // A batch of passes captured once per (system, method, batch size) and
 // replayed.  With kernel timing on, the graph also holds an event node pair
@@ -83,7 +87,7 @@ int pass_graph(tvr_system *sys, int solver, int batch, bool timed, cudaGraphExec
       PassTiming tm;
       tm.graph_nodes = true;
       for (int k = 0; k < TVR_PROF_KINDS; ++k) {
-        tm.slot[k] = ((k != 3 || solver == SOLVER_UPN) && ((sys->profile >> k) & 1) &&
+        tm.slot[k] = (pass_kind(k, solver) && ((sys->profile >> k) & 1) &&
                       i % sys->prof_stride == 0)
                          ? i
                          : -1;
@@ -205,7 +209,7 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   h.b = j.bd;
   for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
   for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
-  h.t2 = sys->t2;
+  h.pg = sys->pg;
   h.w = sys->wplanes[0];
   h.wt = sys->wplanes[1];
   h.hist = j.hist_n > 0 ? sys->hist_dev : nullptr;
@@ -241,7 +245,7 @@ int job_launch(Job &j) {
         if (full)
           if (int rc = prof_harvest(sys)) return rc;
         for (int k = 0; k < TVR_PROF_KINDS; ++k) {
-          const bool used = (k != 3 || j.solver == SOLVER_UPN) && ((sys->profile >> k) & 1);
+          const bool used = pass_kind(k, j.solver) && ((sys->profile >> k) & 1);
           const int sl = used ? prof_take(sys, k, true) : -1;
           tm.slot[k] = sl;
           if (sl >= 0)

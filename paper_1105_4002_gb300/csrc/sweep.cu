@@ -117,9 +117,7 @@ __device__ __forceinline__ void huber_s(const float *x, int ix, int iy, int iz, 
   }
   diff3s(x, ix, iy, iz, n, o.z);
   o.nrm = norm3(o.z);
-  const float den = fmaxf(tau, o.nrm);
-#pragma unroll
-  for (int e = 0; e < 3; ++e) o.w[e] = __fdiv_rn(o.z[e], den);
+  huber_weights(o.z, o.nrm, tau, o.w);
   o.h = huber_h(o.nrm, tau);
 }
 

@@ -39,7 +39,7 @@ struct tvr_system {
   DevState *st = nullptr;
   float *vN[RN_COUNT] = {};
   float *vM[RM_COUNT] = {};
-  float2 *t2 = nullptr;
+  float2 *pg = nullptr;
   float *wplanes[2] = {nullptr, nullptr};  // Huber weight planes (4 N floats each)
   double *hist_dev = nullptr;
   int hist_cap = 0;

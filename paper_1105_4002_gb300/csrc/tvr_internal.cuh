@@ -8,7 +8,7 @@
 #include "tvr.h"
 
 #define TVR_BLOCK 256          // threads per block of every streaming kernel
-#define TVR_RMAX 4             // reductions carried by one kernel
+#define TVR_RMAX 8             // reductions carried by one kernel
 #define TVR_MAX_GRID 4096      // upper bound on blocks of a reducing kernel
 #define TVR_PROF_PAIRS 4096    // timed launches held per kernel kind between harvests
 #define TVR_PROF_KINDS 4       // forward, back projection, step, UPN extrapolation
@@ -84,66 +84,68 @@ __device__ __forceinline__ FF ff_shfl_xor(FF a, int mask) {
   return b;
 }
 
-// Warp-wide reduce-scatter of R <= 4 pairs: after it, the lanes of each group
-// of 32 / P (P = R rounded up to a power of two) hold the warp total of value
-// k = lane / (32 / P).  Each exchange step halves the values a lane carries, so
-// R values cost 2 + 1 + 3 merges (R = 3, 4) instead of 5 R.  ff_merge is
-// commutative, so both partners of an exchange hold the same result.
+// Warp-wide reduce-scatter of R <= 8 pairs (padded to P, a power of two):
+// each exchange step at lane distance 16, 8, ... keeps one half of the values
+// a lane carries and merges the partner's copy of that half, so that after
+// log2 P steps lane l carries value k = l / (32 / P) alone; the remaining
+// steps reduce it within the group of 32 / P lanes.  R values cost
+// (P - 1) + 5 - log2 P merges instead of 5 R.  ff_merge is commutative, so
+// both partners of an exchange hold the same result.
+template <int R>
+struct RedShape {
+  static_assert(R >= 1 && R <= 8, "R");
+  static constexpr int P = R == 1 ? 1 : (R == 2 ? 2 : (R <= 4 ? 4 : 8));
+};
+
 template <int R>
 __device__ __forceinline__ FF warp_reduce_scatter(const FF (&a)[R]) {
-  static_assert(R >= 1 && R <= 4, "R");
+  constexpr int P = RedShape<R>::P;
   const int lane = threadIdx.x & 31;
-  if constexpr (R == 1) {
-    FF v = a[0];
+  FF v[P];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = ff_merge(v, ff_shfl_xor(v, o));
-    return v;
-  } else if constexpr (R == 2) {
-    const bool h16 = lane & 16;
-    FF keep = h16 ? a[1] : a[0];
-    keep = ff_merge(keep, ff_shfl_xor(h16 ? a[0] : a[1], 16));
+  for (int k = 0; k < P; ++k) v[k] = k < R ? a[k < R ? k : 0] : ff_zero();
+  int off = 16;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) keep = ff_merge(keep, ff_shfl_xor(keep, o));
-    return keep;
-  } else {
-    const FF a3 = R == 4 ? a[R - 1] : ff_zero();
-    const bool h16 = lane & 16, h8 = lane & 8;
-    FF k0 = h16 ? a[2] : a[0], k1 = h16 ? a3 : a[1];
-    const FF s0 = h16 ? a[0] : a[2], s1 = h16 ? a[1] : a3;
-    k0 = ff_merge(k0, ff_shfl_xor(s0, 16));
-    k1 = ff_merge(k1, ff_shfl_xor(s1, 16));
-    FF keep = h8 ? k1 : k0;
-    keep = ff_merge(keep, ff_shfl_xor(h8 ? k0 : k1, 8));
+  for (int cnt = P / 2; cnt >= 1; cnt >>= 1, off >>= 1) {
+    const bool hi = lane & off;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) keep = ff_merge(keep, ff_shfl_xor(keep, o));
-    return keep;
-  }
-}
-
-// Block-wide reduction of R pairs; the result is valid in every lane of warp 0.
-// Warps reduce-scatter, then warp 0 holds value k of warp w in lane k W + w
-// (W warps) and reduces within groups of W lanes.
-template <int R>
-__device__ __forceinline__ void block_reduce(FF (&a)[R]) {
-  constexpr int P = R == 1 ? 1 : (R == 2 ? 2 : 4);
-  constexpr int W = TVR_BLOCK / 32;
-  static_assert(P * W <= 32 && (W & (W - 1)) == 0, "block shape");
-  __shared__ FF sh[P][W];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const FF v = warp_reduce_scatter<R>(a);
-  if ((lane & (32 / P - 1)) == 0) sh[lane / (32 / P)][warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    FF u = lane < P * W ? sh[lane / W][lane % W] : ff_zero();
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) u = ff_merge(u, ff_shfl_xor(u, o));
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      a[k].hi = __shfl_sync(0xffffffffu, u.hi, k * W);
-      a[k].lo = __shfl_sync(0xffffffffu, u.lo, k * W);
+    for (int i = 0; i < cnt; ++i) {
+      const FF keep = hi ? v[cnt + i] : v[i];
+      const FF send = hi ? v[i] : v[cnt + i];
+      v[i] = ff_merge(keep, ff_shfl_xor(send, off));
     }
   }
+#pragma unroll
+  for (; off > 0; off >>= 1) v[0] = ff_merge(v[0], ff_shfl_xor(v[0], off));
+  return v[0];
+}
+
+// Block-wide reduction of R pairs; the result is valid in every thread.
+// Warps reduce-scatter; then thread t < P W (W warps) holds value t / W of
+// warp t % W and the groups of W lanes reduce.
+template <int R>
+__device__ __forceinline__ void block_reduce(FF (&a)[R]) {
+  constexpr int P = RedShape<R>::P;
+  constexpr int W = TVR_BLOCK / 32;
+  constexpr int L = 32 / P;
+  constexpr int T2 = (P * W + 31) / 32 * 32;  // threads of the second stage (whole warps)
+  static_assert((W & (W - 1)) == 0 && T2 <= TVR_BLOCK, "block shape");
+  __shared__ FF sh[P][W];
+  __shared__ FF res[P];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const FF v = warp_reduce_scatter<R>(a);
+  if ((lane & (L - 1)) == 0) sh[lane / L][warp] = v;
   __syncthreads();
+  if (threadIdx.x < T2) {
+    const int t = threadIdx.x;
+    FF u = t < P * W ? sh[t / W][t % W] : ff_zero();
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) u = ff_merge(u, ff_shfl_xor(u, o));
+    if (t < P * W && t % W == 0) res[t / W] = u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < R; ++k) a[k] = res[k];
 }
 
 // Grid-wide deterministic reduction.  Every block stores its partial; the last
@@ -216,6 +218,14 @@ __device__ __forceinline__ float norm3(const float z[3]) {
                               __fmul_rn(z[2], z[2])));
 }
 
+// Huber weights of a difference vector z with |z| = nrm: w_e = z_e / max(tau, |z|),
+// as one correctly rounded reciprocal and three products.
+__device__ __forceinline__ void huber_weights(const float z[3], float nrm, float tau, float w[3]) {
+  const float r = __frcp_rn(fmaxf(tau, nrm));
+#pragma unroll
+  for (int e = 0; e < 3; ++e) w[e] = __fmul_rn(z[e], r);
+}
+
 __device__ __forceinline__ void huber_at(const float *__restrict__ x, int ix, int iy, int iz,
                                          int n, float tau, Huber &o) {
   if (ix < 0 || iy < 0 || iz < 0) {
@@ -227,9 +237,7 @@ __device__ __forceinline__ void huber_at(const float *__restrict__ x, int ix, in
   }
   diff3(x, ix, iy, iz, n, o.z);
   o.nrm = norm3(o.z);
-  const float den = fmaxf(tau, o.nrm);
-#pragma unroll
-  for (int e = 0; e < 3; ++e) o.w[e] = __fdiv_rn(o.z[e], den);
+  huber_weights(o.z, o.nrm, tau, o.w);
   o.h = huber_h(o.nrm, tau);
 }
 
@@ -267,12 +275,6 @@ __device__ __forceinline__ float huber_bregman(const float z[3], float nz, const
   return huber_bregman_n(z, nz, zb, norm3(zb), dlt, tau);
 }
 
-// Huber weights of a difference vector z with |z| = nrm: w_e = z_e / max(tau, |z|).
-__device__ __forceinline__ void huber_weights(const float z[3], float nrm, float tau, float w[3]) {
-  const float den = fmaxf(tau, nrm);
-#pragma unroll
-  for (int e = 0; e < 3; ++e) w[e] = __fdiv_rn(z[e], den);
-}
 
 // ---------------------------------------------------------------------------
 // Solver state, resident in device memory.  Control scalars are FP64 and are
@@ -309,7 +311,8 @@ struct DevState {
   // vector roles
   float *vN[RN_COUNT];
   float *vM[RM_COUNT];
-  float2 *t2;  // trial point and step interleaved: (xbar_j, xbar_j - base_j)
+  float2 *pg;  // (p_j, g_j): base point of the next trial and the gradient there,
+               // written by the back projection (solver and init modes)
   // Huber weights w_e(D_j v) of the point v where the next gradient is taken,
   // as 4 planes of N floats: w_0, w_1, w_2 and (w_0 + w_1) + w_2.  `w` holds
   // them for the gradient point (written by the extrapolation kernel in UPN),

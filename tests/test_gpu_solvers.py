@@ -111,9 +111,9 @@ def test_kernel_timing_in_graph_and_direct_modes(c32):
         assert np.array_equal(x, x0) and r.iters == r0.iters
         assert p["forward"][0] == r.f_evals - 1              # one trial forward per f-eval after init
         assert p["backward"][0] == r.g_evals - 1             # one back projection per new point
-        assert p["step"][0] == r.f_evals - 1
+        assert p["step"] == (0, 0.0)                          # fused into the trial forward
         assert p["extrapolation"][0] == r.g_evals - 1
-        assert all(ms > 0 for _, ms in p.values())
+        assert all(ms > 0 for k, (_, ms) in p.items() if k != "step")
 
 
 def test_solves_are_deterministic(c32):
@@ -185,3 +185,33 @@ def test_4cubed_brute_force():
         res = s.solve(method, dev_f32(torch, b), 0.05, 1e-2, 1e-5, x, SolveOptions(k_max=200000))
         assert res.ok, (method, res)
         assert rel_l2(x.cpu().numpy(), ref) <= 1e-3, method
+
+
+@pytest.mark.parametrize("n", [7, 8])
+@pytest.mark.parametrize("method", ["gp", "upn"])
+def test_scalar_and_four_voxel_step_paths(n, method):
+    """Grids with n % 4 != 0 run the one-voxel-per-thread step and extrapolation
+    kernels, n % 4 == 0 the four-voxel ones: both follow the oracle's first
+    iterations and reach its x* at equal eps."""
+    torch = cuda()
+    from gpu_util import oracle_spread
+    from paper_1105_4002_gb300 import SolveOptions, System
+    g = synth.cone_geometry(n, 6, 2 * n - 1, 3.0 * n, 2.0 * n)
+    A = oracle.system_matrix(g)
+    x_true = synth.ellipsoid_phantom(n, 3, (1.0, n / 3.0), (0.2, 1.0), 40 + n)
+    z = synth.standard_normal(g.m, 41 + n)
+    b = oracle.make_data(A, x_true, z, 0.01).astype(np.float32).astype(np.float64)
+    prob = oracle.Problem(A=A, b=b, n=n, alpha=1e-2, tau=1e-4)
+    ref = ORACLE[method](prob, np.zeros(prob.N), 1e-4, oracle.Options(record=True))
+    s = System(g)
+    x = torch.zeros(prob.N, device="cuda")
+    res = s.solve(method, dev_f32(torch, b), prob.alpha, prob.tau, 1e-4, x,
+                  SolveOptions(history=20000))
+    assert res.ok
+    h = res.history
+    for i in range(min(6, len(ref.history), len(h))):
+        assert int(h[i, 5]) == ref.history[i]["trials"], (i, h[i], ref.history[i])
+        assert abs(h[i, 1] - ref.history[i]["gnorm"]) <= 1e-4 * ref.history[i]["gnorm"]
+    _, spread = oracle_spread(prob, ORACLE[method], 1e-4, draws=2)
+    d = rel_l2(x.cpu().numpy(), ref.x)
+    assert d <= max(XSTAR_TOL, 3 * spread), (d, spread)
