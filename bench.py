@@ -586,11 +586,12 @@ def main():
     # the four Huber weight planes, x read and g and (p, g) written
     bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
     # trial forward with the fused step: A (values + indices), row pointers, the
-    # (p, g) pairs, b, r and A d (UPN) rows, xbar written, and for GPBB trials
-    # the four Huber weight planes (weighted by the share of GPBB trials)
+    # (p, g) pairs read and xbar written, b read and r written; A d written in
+    # UPN trials, the four Huber weight planes in GPBB trials (weighted by the
+    # share of each method's trials among the timed launches)
     w_share = trials_gpbb / max(trials_gpbb + trials_upn, 1)
-    bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 3 * 4 * m + extra_m * m
-                 + w_share * 16 * N)
+    bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
+                 + w_share * 16 * N + (1 - w_share) * 4 * m)
     peak, peak_kind = measured_peak_gbs()
     roof = None
     nf, msf = prof["forward"]

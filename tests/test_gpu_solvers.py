@@ -189,9 +189,9 @@ def test_4cubed_brute_force():
 
 @pytest.mark.parametrize("n", [7, 8])
 @pytest.mark.parametrize("method", ["gp", "upn"])
-def test_scalar_and_four_voxel_step_paths(n, method):
-    """Grids with n % 4 != 0 run the one-voxel-per-thread step and extrapolation
-    kernels, n % 4 == 0 the four-voxel ones: both follow the oracle's first
+def test_small_grids_of_odd_and_even_edge(n, method):
+    """On 7^3 and 8^3 grids (ragged and whole 4-voxel x-rows, voxel index
+    decomposition by invariant divisors) the solvers follow the oracle's first
     iterations and reach its x* at equal eps."""
     torch = cuda()
     from gpu_util import oracle_spread
