@@ -57,10 +57,20 @@ typedef enum tvr_geometry_kind {
 
 typedef enum tvr_storage {
   TVR_STORAGE_FP32 = 0,         /* CSR and CSC, float32 values, int32 indices, int64 pointers */
-  TVR_STORAGE_BF16_ROWSCALE = 1 /* values a_ij = s_i q_ij: per-row FP32 scale s_i = max_j a_ij and
+  TVR_STORAGE_BF16_ROWSCALE = 1, /* values a_ij = s_i q_ij: per-row FP32 scale s_i = max_j a_ij and
                                    bfloat16 codes q_ij = bf16(a_ij / s_i) (round to nearest even),
                                    the same codes in CSR and CSC; FP32 accumulation; the back
                                    projection applies exactly the transpose of the forward matrix */
+  TVR_STORAGE_MATRIX_FREE = 2   /* no stored A: every projection computes its entries on the fly as
+                                   the float32 length of the ray segment (source to pixel centre)
+                                   inside the voxel's unit box, from float32 view constants; the
+                                   forward (per ray, walking the slabs of its major axis) and the
+                                   back projection (per voxel, over the pixels of its projected
+                                   footprint) evaluate the same entry function, so they are exact
+                                   transposes.  The entries differ from the FP64 Siddon lengths of
+                                   the stored kinds by the float32 rounding of the ray geometry.
+                                   Not available: CSR/CSC export, the FP64 and allocation-free
+                                   entry points, tvr_solve_sweep */
 } tvr_storage;
 
 /* Number of doubles per view record. */

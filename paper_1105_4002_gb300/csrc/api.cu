@@ -112,7 +112,8 @@ int tvr_system_free(tvr_system *sys) {
 int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_system **out) {
   if (!g || !out) return fail(TVR_ERR_ARG, "tvr_build_system: null argument");
   *out = nullptr;
-  if (storage != TVR_STORAGE_FP32 && storage != TVR_STORAGE_BF16_ROWSCALE)
+  if (storage != TVR_STORAGE_FP32 && storage != TVR_STORAGE_BF16_ROWSCALE &&
+      storage != TVR_STORAGE_MATRIX_FREE)
     return fail(TVR_ERR_ARG, "tvr_build_system: unknown storage");
   if (g->n < 1 || g->n_views < 1 || g->det_cols < 1 || g->det_rows < 1 || !g->views ||
       (g->kind != TVR_CONE && g->kind != TVR_PARALLEL) || g->reserved != 0)
@@ -151,9 +152,14 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   const size_t vbytes = sizeof(double) * TVR_VIEW_FIELDS * g->n_views;
   BUILD_CUDA(cudaMalloc(&views_dev, vbytes));
   BUILD_CUDA(cudaMemcpyAsync(views_dev, g->views, vbytes, cudaMemcpyHostToDevice, s));
-  BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
-  if (storage == TVR_STORAGE_BF16_ROWSCALE) BUILD_CUDA(quantize_bf16(sys->A, s));
-  BUILD_CUDA(interleave_lanes(sys->A, s));
+  if (storage == TVR_STORAGE_MATRIX_FREE) {
+    BUILD_CUDA(build_matrix_free(views_dev, g->n, g->n_views, g->det_cols, g->det_rows, g->kind,
+                                 m, N, sys->A, s));
+  } else {
+    BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
+    if (storage == TVR_STORAGE_BF16_ROWSCALE) BUILD_CUDA(quantize_bf16(sys->A, s));
+    BUILD_CUDA(interleave_lanes(sys->A, s));
+  }
   sys->nnz = sys->A.nnz;
   // reduction workspace: per slot partials + counter + outputs
   const size_t part = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;
@@ -188,6 +194,8 @@ int tvr_system_shape(const tvr_system *sys, int64_t *m, int64_t *N, int64_t *nnz
 
 int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col, float *val) {
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
+  if (sys->A.storage == TVR_STORAGE_MATRIX_FREE)
+    return fail(TVR_ERR_ARG, "export: a matrix-free system stores no matrix");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
   const float *vd = sys->A.val;
@@ -209,6 +217,8 @@ int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col,
 
 int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row, float *val) {
   if (!sys) return fail(TVR_ERR_ARG, "export: null system");
+  if (sys->A.storage == TVR_STORAGE_MATRIX_FREE)
+    return fail(TVR_ERR_ARG, "export: a matrix-free system stores no matrix");
   TVR_CUDA(cudaSetDevice(sys->device));
   TVR_CUDA(cudaDeviceSynchronize());
   const float *vd = sys->A.cval;

@@ -18,6 +18,7 @@
 
 #include <vector>
 
+#include "mf.cuh"
 #include "tvr_internal.cuh"
 
 namespace {
@@ -461,7 +462,7 @@ cudaError_t transpose(MatStore &A, cudaStream_t s) {
 
 void free_matrix(MatStore &A) {
   void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col,   A.row,
-                  A.val,     A.cval,    A.qval,    A.qcval,   A.rscale};
+                  A.val,     A.cval,    A.qval,    A.qcval,   A.rscale, A.mfv};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   A = MatStore{};
@@ -513,6 +514,69 @@ cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kin
   if (A.nnz_pad == 0) return cudaStreamSynchronize(s);
   if (A.nnz_pad >= ((int64_t)1 << 31)) return transpose<int64_t>(A, s);
   return transpose<int32_t>(A, s);
+}
+
+// ---- matrix-free storage: float32 view constants ----
+namespace {
+
+// One thread per view: the FP64 record rounded to float32, the detector
+// normal (oriented away from the source) and the dual basis of (u, w) in the
+// detector plane, all formed in FP64 with explicit rounding.
+__global__ void k_mf_views(const ViewRec *__restrict__ views, int V, MfView *__restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double *r = views[v].v;
+  const double *src = r, *det = r + 3, *u = r + 6, *w = r + 9;
+  double nr[3] = {dsub(dmul(u[1], w[2]), dmul(u[2], w[1])), dsub(dmul(u[2], w[0]), dmul(u[0], w[2])),
+                  dsub(dmul(u[0], w[1]), dmul(u[1], w[0]))};
+  const double nn = __dsqrt_rn(dadd(dadd(dmul(nr[0], nr[0]), dmul(nr[1], nr[1])), dmul(nr[2], nr[2])));
+  double dn = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    nr[k] = nn > 0.0 ? ddiv(nr[k], nn) : 0.0;
+    dn = dadd(dn, dmul(dsub(det[k], src[k]), nr[k]));
+  }
+  if (dn < 0.0) {
+    for (int k = 0; k < 3; ++k) nr[k] = -nr[k];
+    dn = -dn;
+  }
+  const double guu = dadd(dadd(dmul(u[0], u[0]), dmul(u[1], u[1])), dmul(u[2], u[2]));
+  const double gww = dadd(dadd(dmul(w[0], w[0]), dmul(w[1], w[1])), dmul(w[2], w[2]));
+  const double guw = dadd(dadd(dmul(u[0], w[0]), dmul(u[1], w[1])), dmul(u[2], w[2]));
+  const double g = dsub(dmul(guu, gww), dmul(guw, guw));
+  MfView o;
+  for (int k = 0; k < 3; ++k) {
+    o.src[k] = (float)src[k];
+    o.det[k] = (float)det[k];
+    o.u[k] = (float)u[k];
+    o.w[k] = (float)w[k];
+    o.nrm[k] = (float)nr[k];
+    o.uu[k] = g > 0.0 ? (float)ddiv(dsub(dmul(gww, u[k]), dmul(guw, w[k])), g) : 0.f;
+    o.ww[k] = g > 0.0 ? (float)ddiv(dsub(dmul(guu, w[k]), dmul(guw, u[k])), g) : 0.f;
+  }
+  o.dn = (float)dn;
+  o.pad[0] = o.pad[1] = 0.f;
+  out[v] = o;
+}
+
+}  // namespace
+
+// Matrix-free storage: only the view constants.  Synchronises `s`.
+cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int Pv, int kind,
+                              int64_t m, int64_t N, MatStore &A, cudaStream_t s) {
+  A = MatStore{};
+  A.m = m;
+  A.N = N;
+  A.storage = TVR_STORAGE_MATRIX_FREE;
+  A.V = V;
+  A.Pu = Pu;
+  A.Pv = Pv;
+  A.kind = kind;
+  (void)n;
+  BM_TRY(owned(&A.mfv, V));
+  k_mf_views<<<(V + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), V,
+                                              A.mfv);
+  BM_TRY(cudaGetLastError());
+  return cudaStreamSynchronize(s);
 }
 
 // ---- BF16 storage with per-row scale ----

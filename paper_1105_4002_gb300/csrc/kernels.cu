@@ -16,6 +16,7 @@
 #include <utility>
 
 #include "ctrl.cuh"
+#include "mf.cuh"
 #include "tvr_internal.cuh"
 
 #define FULL 0xffffffffu
@@ -111,8 +112,8 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // Forward projection.  G lanes per row, rows of a warp are consecutive (rays
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool BF>
-__global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
+template <int G, int MODE, bool BF, bool MF = false>
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
               float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1,
               float *__restrict__ rsout = nullptr) {
@@ -150,11 +151,30 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
     const int64_t row = base + sub;
     const bool valid = row < A.m;
     int64_t beg = 0, end = 0;
-    if (valid) {
+    if (valid && !MF) {
       beg = __ldg(A.row_ptr + row);
       end = __ldg(A.row_ptr + row + 1);
     }
     float sx = 0.f, sd = 0.f;
+    if (MF && valid) {
+      // matrix-free: the entries of the row from the ray geometry (mf.cuh)
+      const int64_t per = (int64_t)A.Pu * A.Pv;
+      const int vi = (int)(row / per);
+      const int64_t rem = row - (int64_t)vi * per;
+      const int q = (int)(rem / A.Pu), pp = (int)(rem - (int64_t)q * A.Pu);
+      MfRay ray;
+      mf_pixel_ray(A.mfv[vi], A.kind, A.Pu, A.Pv, pp, q, ray);
+      mf_row<G>(ray, A.n, lane, [&](int c, float v) {
+        if (MODE == FWD_TRIAL) {
+          const float2 qc = __ldg(pg + c);
+          const float bc = xbar_of(qc.x, qc.y, s);
+          sx = __fmaf_rn(v, bc, sx);
+          sd = __fmaf_rn(v, __fsub_rn(bc, qc.x), sd);
+        } else {
+          sx = __fmaf_rn(v, __ldg(x + c), sx);
+        }
+      });
+    }
     // Rows are padded to multiples of 4 entries: each lane reads 4 entries
     // with one 16-byte load of indices and one of values, then gathers.
     // Trial mode gathers (xbar_j, xbar_j - p_j) pairs with one 8-byte load.
@@ -288,8 +308,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_FWD_MIN_BLOCKS)
 // lanes 0..3 of a group evaluate the Huber weights of voxels j, j-ex, j-ey,
 // j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool BF>
-__global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
+template <int G, int MODE, bool BF, bool MF = false>
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
                const double *__restrict__ data_in, double *phi_dev, DevState *st,
@@ -336,12 +356,12 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
     const int64_t j = base + sub;
     const bool valid = j < A.N;
     int64_t beg = 0, end = 0;
-    if (valid) {
+    if (valid && !MF) {
       beg = __ldg(A.col_ptr + j);
       end = __ldg(A.col_ptr + j + 1);
     }
     int ix = 0, iy = 0, iz = 0;
-    if (MODE != BWD_ADJ) voxel_of(A, valid ? j : 0, ix, iy, iz);
+    if (MODE != BWD_ADJ || MF) voxel_of(A, valid ? j : 0, ix, iy, iz);
     // solver mode: this lane's term of [grad TV_tau]_j from the Huber weight
     // planes (lane 0: -(w_0 + w_1 + w_2) at j; lanes 1..3: w_e at j - e),
     // loaded ahead of the projection loop
@@ -358,6 +378,11 @@ __global__ void __launch_bounds__(TVR_BLOCK, TVR_BWD_MIN_BLOCKS)
         c = iz > 0 ? __ldg(W + 2 * A.N + j - nn) : 0.f;
     }
     float s = 0.f;
+    if (MF && valid) {
+      // matrix-free: the entries of the column from the view geometry (mf.cuh)
+      mf_column<G>(A.mfv, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
+                   [&](int64_t i, float v) { s = __fmaf_rn(v, __ldg(r + i), s); });
+    }
     for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kColChunks) {
       int4 i4[kColChunks];
       float4 v4[kColChunks];
@@ -646,11 +671,13 @@ void launch_pdl(void (*kernel)(P...), int grid, cudaStream_t s, A &&...args) {
 // Kernel instance for the system's storage (float32 or bfloat16 values).
 template <int MODE>
 auto fwd_kernel(const MatDev &A) {
-  return A.bf16 ? k_forward<kRowLanes, MODE, true> : k_forward<kRowLanes, MODE, false>;
+  return A.mf ? k_forward<kRowLanes, MODE, false, true>
+              : (A.bf16 ? k_forward<kRowLanes, MODE, true> : k_forward<kRowLanes, MODE, false>);
 }
 template <int MODE>
 auto bwd_kernel(const MatDev &A) {
-  return A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>;
+  return A.mf ? k_backward<kColLanes, MODE, false, true>
+              : (A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>);
 }
 
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,

@@ -1,0 +1,229 @@
+// Matrix-free projector: the entries of A computed on the fly from the scan
+// geometry instead of read from the stored CSR / CSC arrays.
+//
+// Sec. II-A defines A only as the operator that maps the image to ray sums;
+// the entry a_ij is the length of ray i inside voxel j.  Here that length is
+// the intersection of the ray segment (source to pixel centre) with the unit
+// box of voxel j (the slab method), evaluated in float32 from per-view float32
+// constants.  One function, mf_len, gives a_ij for both directions:
+//   forward  (row i):    walk the slabs of the ray's major axis, take the
+//                        2-4 candidate voxels of each slab, keep len > 0;
+//   adjoint  (column j): for each view, take the pixels inside the bounding
+//                        box of the voxel's projected corners, keep len > 0.
+// Both enumerations are conservative (a margin of 1e-3 voxel / pixel), so the
+// two projections apply exactly the same matrix and are exact transposes of
+// each other; they differ from the FP64 Siddon lengths of the stored matrix
+// by the float32 rounding of the ray geometry (about 2^-24 of the source and
+// detector distances per coordinate).
+//
+// A ray parallel to a grid axis keeps the voxels with lo <= s < lo + 1 on that
+// axis (the voxel of the midpoint, as in the stored matrix) and, like the
+// stored matrix, no voxel when it lies on the volume's lower boundary face.
+#pragma once
+
+#include "tvr_internal.cuh"
+
+// Per-view constants (float32).  Pixel (p, q) has centre det + a u + b w with
+// a = p - (Pu - 1)/2, b = q - (Pv - 1)/2; a cone-beam ray starts at src, a
+// parallel-beam ray at src + a u + b w.  nrm is oriented so that dn > 0.
+struct MfView {
+  float src[3], det[3], u[3], w[3];
+  float nrm[3];       // unit normal of the detector plane
+  float uu[3], ww[3]; // u / |u|^2 and w / |w|^2: pixel coordinates of a detector-plane offset
+  float dn;           // (det - src) . nrm
+  float pad[2];
+};
+
+struct MfRay {
+  float s[3], d[3], inv[3];  // start, d = end - start, 1 / d (0 where |d| <= 1e-30: parallel)
+  float dn;                  // |d|
+};
+
+__device__ __forceinline__ float mf_half(int n) { return 0.5f * (float)n; }
+
+__device__ __forceinline__ void mf_pixel_ray(const MfView &v, int kind, int Pu, int Pv, int p,
+                                             int q, MfRay &r) {
+  const float a = __fsub_rn((float)p, 0.5f * (float)(Pu - 1));
+  const float b = __fsub_rn((float)q, 0.5f * (float)(Pv - 1));
+  float dd = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float au = __fmul_rn(a, v.u[k]), bw = __fmul_rn(b, v.w[k]);
+    const float c = __fadd_rn(__fadd_rn(v.det[k], au), bw);
+    r.s[k] = kind == TVR_PARALLEL ? __fadd_rn(__fadd_rn(v.src[k], au), bw) : v.src[k];
+    r.d[k] = __fsub_rn(c, r.s[k]);
+    r.inv[k] = fabsf(r.d[k]) > 1e-30f ? __frcp_rn(r.d[k]) : 0.f;
+    dd = __fadd_rn(dd, __fmul_rn(r.d[k], r.d[k]));
+  }
+  r.dn = __fsqrt_rn(dd);
+}
+
+// Length of ray r inside voxel (ix, iy, iz): the intersection of t in [0, 1]
+// with the three slabs of the voxel's box, times |d|.
+__device__ __forceinline__ float mf_len(const MfRay &r, int ix, int iy, int iz, float half) {
+  const int id[3] = {ix, iy, iz};
+  float te = 0.f, tx = 1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float lo = __fsub_rn((float)id[k], half);
+    if (r.inv[k] != 0.f) {
+      const float t0 = __fmul_rn(__fsub_rn(lo, r.s[k]), r.inv[k]);
+      const float t1 = __fmul_rn(__fsub_rn(__fadd_rn(lo, 1.f), r.s[k]), r.inv[k]);
+      te = fmaxf(te, fminf(t0, t1));
+      tx = fminf(tx, fmaxf(t0, t1));
+    } else if (!(r.s[k] > -half && r.s[k] >= lo && r.s[k] < __fadd_rn(lo, 1.f))) {
+      return 0.f;
+    }
+  }
+  return tx > te ? __fmul_rn(__fsub_rn(tx, te), r.dn) : 0.f;
+}
+
+// Calls use(j, a_ij) for every voxel j with a_ij > 0 in the slabs
+// k = k0 + lane, k0 + lane + G, ... of the ray's major axis.
+template <int G, typename Use>
+__device__ __forceinline__ void mf_row(const MfRay &r, int n, int lane, Use &&use) {
+  const float half = mf_half(n);
+  // parameter range inside the volume box (the forward walk only; mf_len
+  // decides every entry)
+  float te = 0.f, tx = 1.f;
+  int ax = 0;
+  float best = -1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ad = fabsf(r.d[k]);
+    if (ad > best) {
+      best = ad;
+      ax = k;
+    }
+    if (r.inv[k] != 0.f) {
+      const float t0 = __fmul_rn(__fsub_rn(-half, r.s[k]), r.inv[k]);
+      const float t1 = __fmul_rn(__fsub_rn(half, r.s[k]), r.inv[k]);
+      te = fmaxf(te, fminf(t0, t1));
+      tx = fminf(tx, fmaxf(t0, t1));
+    } else if (!(r.s[k] > -half && r.s[k] < half)) {
+      return;
+    }
+  }
+  // components along the major axis and the two others (selects, not
+  // dynamic indexing, so the ray stays in registers)
+  auto pick = [ax](const float v[3], int which) {
+    // which = 0: major axis; 1: first other axis; 2: second other axis
+    const int k = which == 0 ? ax : (which == 1 ? (ax == 0 ? 1 : 0) : (ax == 2 ? 1 : 2));
+    return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
+  };
+  const float sA = pick(r.s, 0), dA = pick(r.d, 0), iA = pick(r.inv, 0);
+  const float s1 = pick(r.s, 1), d1 = pick(r.d, 1);
+  const float s2 = pick(r.s, 2), d2 = pick(r.d, 2);
+  if (!(tx > te) || iA == 0.f) return;
+  // slab range of the major axis covered by [te, tx] (one slab of margin)
+  const float ca = __fadd_rn(__fadd_rn(sA, __fmul_rn(te, dA)), half);
+  const float cb = __fadd_rn(__fadd_rn(sA, __fmul_rn(tx, dA)), half);
+  int k0 = (int)floorf(fminf(ca, cb)) - 1, k1 = (int)floorf(fmaxf(ca, cb)) + 1;
+  k0 = k0 < 0 ? 0 : k0;
+  k1 = k1 > n - 1 ? n - 1 : k1;
+  constexpr float kMargin = 1e-3f;
+  for (int k = k0 + lane; k <= k1; k += G) {
+    // parameters of the slab's two planes, clipped to the volume range
+    const float p0 = __fmul_rn(__fsub_rn(__fsub_rn((float)k, half), sA), iA);
+    const float p1 = __fmul_rn(__fsub_rn(__fsub_rn((float)(k + 1), half), sA), iA);
+    const float ta = fmaxf(te, fminf(p0, p1)), tb = fminf(tx, fmaxf(p0, p1));
+    if (!(tb >= ta)) continue;
+    const float c10 = __fadd_rn(__fadd_rn(s1, __fmul_rn(ta, d1)), half);
+    const float c11 = __fadd_rn(__fadd_rn(s1, __fmul_rn(tb, d1)), half);
+    const float c20 = __fadd_rn(__fadd_rn(s2, __fmul_rn(ta, d2)), half);
+    const float c21 = __fadd_rn(__fadd_rn(s2, __fmul_rn(tb, d2)), half);
+    int lo1 = (int)floorf(fminf(c10, c11) - kMargin), hi1 = (int)floorf(fmaxf(c10, c11) + kMargin);
+    int lo2 = (int)floorf(fminf(c20, c21) - kMargin), hi2 = (int)floorf(fmaxf(c20, c21) + kMargin);
+    lo1 = lo1 < 0 ? 0 : lo1;
+    lo2 = lo2 < 0 ? 0 : lo2;
+    hi1 = hi1 > n - 1 ? n - 1 : hi1;
+    hi2 = hi2 > n - 1 ? n - 1 : hi2;
+    for (int i2 = lo2; i2 <= hi2; ++i2)
+      for (int i1 = lo1; i1 <= hi1; ++i1) {
+        const int ix = ax == 0 ? k : i1;
+        const int iy = ax == 1 ? k : (ax == 0 ? i1 : i2);
+        const int iz = ax == 2 ? k : i2;
+        const float len = mf_len(r, ix, iy, iz, half);
+        if (len > 0.f) use((int)(ix + n * (iy + n * iz)), len);
+      }
+  }
+}
+
+// Calls use(i, a_ij) for every ray i with a_ij > 0 of the views
+// v = lane, lane + G, ... for voxel (ix, iy, iz).
+template <int G, typename Use>
+__device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int V, int kind, int Pu,
+                                          int Pv, int n, int ix, int iy, int iz, int lane,
+                                          Use &&use) {
+  const float half = mf_half(n);
+  constexpr float kMargin = 1e-3f;
+  const float ca = 0.5f * (float)(Pu - 1), cb = 0.5f * (float)(Pv - 1);
+  for (int vi = lane; vi < V; vi += G) {
+    const MfView &v = views[vi];
+    // pixel-coordinate box of the projected corners
+    float amin = 3.4e38f, amax = -3.4e38f, bmin = 3.4e38f, bmax = -3.4e38f;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float X[3] = {__fsub_rn((float)(ix + (c & 1)), half),
+                          __fsub_rn((float)(iy + ((c >> 1) & 1)), half),
+                          __fsub_rn((float)(iz + ((c >> 2) & 1)), half)};
+      float P[3];
+      if (kind == TVR_PARALLEL) {
+        // along the common direction det - src onto the detector plane
+        float dir[3], num = 0.f, den = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          dir[k] = __fsub_rn(v.det[k], v.src[k]);
+          num = __fadd_rn(num, __fmul_rn(__fsub_rn(v.det[k], X[k]), v.nrm[k]));
+          den = __fadd_rn(den, __fmul_rn(dir[k], v.nrm[k]));
+        }
+        const float t = __fdiv_rn(num, den);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P[k] = __fadd_rn(X[k], __fmul_rn(t, dir[k]));
+      } else {
+        // central projection from the source onto the detector plane
+        float e[3], den = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          e[k] = __fsub_rn(X[k], v.src[k]);
+          den = __fadd_rn(den, __fmul_rn(e[k], v.nrm[k]));
+        }
+        ok = ok && den > 0.f;  // a corner at or behind the source plane: use the whole detector
+        const float t = __fdiv_rn(v.dn, den);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P[k] = __fadd_rn(v.src[k], __fmul_rn(t, e[k]));
+      }
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float o = __fsub_rn(P[k], v.det[k]);
+        a = __fadd_rn(a, __fmul_rn(o, v.uu[k]));
+        b = __fadd_rn(b, __fmul_rn(o, v.ww[k]));
+      }
+      amin = fminf(amin, a);
+      amax = fmaxf(amax, a);
+      bmin = fminf(bmin, b);
+      bmax = fmaxf(bmax, b);
+    }
+    int p0 = 0, p1 = Pu - 1, q0 = 0, q1 = Pv - 1;  // whole detector unless the box is sound
+    const float lim = 1e7f;
+    if (ok && fabsf(amin) < lim && fabsf(amax) < lim && fabsf(bmin) < lim && fabsf(bmax) < lim) {
+      p0 = (int)ceilf(__fadd_rn(amin, ca) - kMargin);
+      p1 = (int)floorf(__fadd_rn(amax, ca) + kMargin);
+      q0 = (int)ceilf(__fadd_rn(bmin, cb) - kMargin);
+      q1 = (int)floorf(__fadd_rn(bmax, cb) + kMargin);
+      p0 = p0 < 0 ? 0 : p0;
+      q0 = q0 < 0 ? 0 : q0;
+      p1 = p1 > Pu - 1 ? Pu - 1 : p1;
+      q1 = q1 > Pv - 1 ? Pv - 1 : q1;
+    }
+    for (int q = q0; q <= q1; ++q)
+      for (int p = p0; p <= p1; ++p) {
+        MfRay r;
+        mf_pixel_ray(v, kind, Pu, Pv, p, q, r);
+        const float len = mf_len(r, ix, iy, iz, half);
+        if (len > 0.f) use(((int64_t)vi * Pv + q) * Pu + p, len);
+      }
+  }
+}

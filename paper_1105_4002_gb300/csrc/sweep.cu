@@ -552,6 +552,8 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   tvr_system *sys = const_cast<tvr_system *>(csys);
   if (!sys || !b || !alphas || !X) return fail(TVR_ERR_ARG, "tvr_solve_sweep: null argument");
   if (k < 1 || k > KS) return fail(TVR_ERR_ARG, "tvr_solve_sweep: need 1 <= k <= 8");
+  if (sys->A.storage == TVR_STORAGE_MATRIX_FREE)
+    return fail(TVR_ERR_ARG, "tvr_solve_sweep: needs a stored matrix (FP32 or BF16 storage)");
   if (method != SOLVER_GP && method != SOLVER_GPBB && method != SOLVER_UPN)
     return fail(TVR_ERR_ARG, "tvr_solve_sweep: method must be 1 (GP), 2 (GPBB) or 3 (UPN)");
   for (int c = 0; c < k; ++c)

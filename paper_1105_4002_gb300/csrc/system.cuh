@@ -84,6 +84,12 @@ struct tvr_system {
     d.qval = A.qval;
     d.qcval = A.qcval;
     d.rscale = A.rscale;
+    d.mf = A.storage == TVR_STORAGE_MATRIX_FREE;
+    d.mfv = A.mfv;
+    d.V = A.V;
+    d.Pu = A.Pu;
+    d.Pv = A.Pv;
+    d.kind = A.kind;
     return d;
   }
 };

@@ -352,6 +352,8 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t u, const FastDiv &f) {
   return (__umulhi(u, f.m) + u) >> f.l;
 }
 
+struct MfView;  // matrix-free view constants (mf.cuh)
+
 struct MatDev {
   int n;
   FastDiv div_n, div_nn;   // divisors n and n^2 of the voxel index
@@ -367,6 +369,10 @@ struct MatDev {
   const __nv_bfloat16 *qval;   // CSR codes [stored]
   const __nv_bfloat16 *qcval;  // CSC codes [stored]
   const float *rscale;         // [m]
+  // matrix-free storage: no arrays above; view constants and scan shape
+  int mf;
+  const MfView *mfv;
+  int V, Pu, Pv, kind;
 };
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -472,6 +478,8 @@ struct MatStore {
   int storage = TVR_STORAGE_FP32;
   __nv_bfloat16 *qval = nullptr, *qcval = nullptr;  // BF16 codes (null for FP32)
   float *rscale = nullptr;                          // BF16 per-row scales [m]
+  MfView *mfv = nullptr;                            // matrix-free view constants [V]
+  int V = 0, Pu = 0, Pv = 0, kind = 0;
 };
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
                                cudaStream_t s);
@@ -479,6 +487,8 @@ int64_t scan_tmp_len(int64_t n);
 cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
                          int64_t N, MatStore &A, cudaStream_t s);
 cudaError_t quantize_bf16(MatStore &A, cudaStream_t s);
+cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int Pv, int kind,
+                              int64_t m, int64_t N, MatStore &A, cudaStream_t s);
 cudaError_t interleave_lanes(MatStore &A, cudaStream_t s);
 cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s);
 void free_matrix(MatStore &A);
