@@ -17,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import tv
-from ._siddon import build, row, system_matrix, trace_ray
+from ._siddon import adjoint, build, forward, row, system_matrix, trace_ray
 from .objective import Problem, gradient_map, project_Q
 from .solvers import (ERR_LINESEARCH, ERR_NONFINITE, NOT_CONVERGED, OK, Options, Result,
                       solve_gp, solve_gpbb, solve_upn, upn_theta_next)
@@ -47,7 +47,7 @@ def problem_from_config(cfg, alpha=None, tau=None):
 
 
 __all__ = [
-    "build", "row", "system_matrix", "trace_ray", "tv", "Problem", "gradient_map",
+    "adjoint", "build", "forward", "row", "system_matrix", "trace_ray", "tv", "Problem", "gradient_map",
     "project_Q", "Options", "Result", "solve_gp", "solve_gpbb", "solve_upn", "upn_theta_next",
     "make_data", "problem_from_config", "OK", "NOT_CONVERGED", "ERR_LINESEARCH", "ERR_NONFINITE",
 ]

@@ -16,8 +16,9 @@ _SRC = os.path.join(_HERE, "siddon.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # -ffp-contract=off: no fused multiply-add, every operation rounds on its own
-# (gcc contracts by default on aarch64).
-CFLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+# (gcc contracts by default on aarch64).  OpenMP spreads the ray-by-ray
+# projections (forward, adjoint) over the host cores.
+CFLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
@@ -46,6 +47,10 @@ def lib():
         L.orc_siddon_fill.argtypes = [ctypes.c_int] * 5 + [P, P, P, P]
         L.orc_siddon_row.restype = ctypes.c_int64
         L.orc_siddon_row.argtypes = [ctypes.c_int] * 4 + [P, ctypes.c_int64, P, P]
+        L.orc_forward.restype = None
+        L.orc_forward.argtypes = [ctypes.c_int] * 5 + [P, P, P]
+        L.orc_adjoint.restype = None
+        L.orc_adjoint.argtypes = [ctypes.c_int] * 5 + [P, P, P]
         _lib = L
     return _lib
 
@@ -93,3 +98,25 @@ def row(geom, i: int):
     k = lib().orc_siddon_row(n, geom.det_cols, geom.det_rows, geom.kind, _ptr(views), int(i),
                              _ptr(cols), _ptr(vals))
     return cols[:k].copy(), vals[:k].copy()
+
+
+def forward(geom, x) -> np.ndarray:
+    """A x (FP64) computed ray by ray without storing A."""
+    views = np.ascontiguousarray(geom.views, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.size == geom.N
+    y = np.zeros(geom.m, dtype=np.float64)
+    lib().orc_forward(geom.n, geom.n_views, geom.det_cols, geom.det_rows, geom.kind, _ptr(views),
+                      _ptr(x), _ptr(y))
+    return y
+
+
+def adjoint(geom, r) -> np.ndarray:
+    """A^T r (FP64) computed ray by ray without storing A."""
+    views = np.ascontiguousarray(geom.views, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    assert r.size == geom.m
+    z = np.zeros(geom.N, dtype=np.float64)
+    lib().orc_adjoint(geom.n, geom.n_views, geom.det_cols, geom.det_rows, geom.kind, _ptr(views),
+                      _ptr(r), _ptr(z))
+    return z

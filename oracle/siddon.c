@@ -21,6 +21,10 @@
  * Compile with -ffp-contract=off: every product and sum is rounded on its own.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -174,4 +178,79 @@ int64_t orc_siddon_row(int n, int Pu, int Pv, int kind, const double *views, int
   double s[3], c[3];
   ray_endpoints(views + (int64_t)v * VIEW_FIELDS, kind, Pu, Pv, p, q, s, c);
   return orc_trace_ray(s, c, n, cols, vals);
+}
+
+/* y = A x without storing A, for volumes whose A does not fit in RAM: each
+   row's entries in traversal order, summed in FP64 (Sec. II-A: A x is the
+   vector of ray sums of x).  Rays are independent; with OpenMP they are
+   spread over threads, each row still summed in its own order. */
+void orc_forward(int n, int V, int Pu, int Pv, int kind, const double *views, const double *x,
+                 double *y) {
+  const int64_t m = (int64_t)V * Pu * Pv;
+#pragma omp parallel
+  {
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (3 * (size_t)n + 4));
+    double *vals = (double *)malloc(sizeof(double) * (3 * (size_t)n + 4));
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t i = 0; i < m; ++i) {
+      const int64_t per = (int64_t)Pu * Pv;
+      const int v = (int)(i / per);
+      const int64_t rem = i - (int64_t)v * per;
+      const int q = (int)(rem / Pu), p = (int)(rem - (int64_t)q * Pu);
+      double s[3], c[3];
+      ray_endpoints(views + (int64_t)v * VIEW_FIELDS, kind, Pu, Pv, p, q, s, c);
+      const int64_t k = orc_trace_ray(s, c, n, cols, vals);
+      double acc = 0.0;
+      for (int64_t e = 0; e < k; ++e) acc += vals[e] * x[cols[e]];
+      y[i] = acc;
+    }
+    free(cols);
+    free(vals);
+  }
+}
+
+/* z = A^T r without storing A: every ray i adds r_i a_ij to z_j for its
+   entries, in FP64.  With OpenMP each thread accumulates the rays of its
+   share into its own copy of z and the copies are added in thread order, so
+   the rounding depends on the number of threads (not on scheduling). */
+void orc_adjoint(int n, int V, int Pu, int Pv, int kind, const double *views, const double *r,
+                 double *z) {
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t m = (int64_t)V * Pu * Pv;
+  for (int64_t j = 0; j < N; ++j) z[j] = 0.0;
+  int nt = 1;
+#ifdef _OPENMP
+  nt = omp_get_max_threads();
+#endif
+  double **part = (double **)calloc((size_t)nt, sizeof(double *));
+#pragma omp parallel num_threads(nt)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    double *zt = (double *)calloc((size_t)N, sizeof(double));
+    part[t] = zt;
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (3 * (size_t)n + 4));
+    double *vals = (double *)malloc(sizeof(double) * (3 * (size_t)n + 4));
+    /* static split: thread t takes one contiguous block of rays */
+    const int64_t lo = m * t / nt, hi = m * (t + 1) / nt;
+    for (int64_t i = lo; i < hi; ++i) {
+      const int64_t per = (int64_t)Pu * Pv;
+      const int v = (int)(i / per);
+      const int64_t rem = i - (int64_t)v * per;
+      const int q = (int)(rem / Pu), p = (int)(rem - (int64_t)q * Pu);
+      double s[3], c[3];
+      ray_endpoints(views + (int64_t)v * VIEW_FIELDS, kind, Pu, Pv, p, q, s, c);
+      const int64_t k = orc_trace_ray(s, c, n, cols, vals);
+      for (int64_t e = 0; e < k; ++e) zt[cols[e]] += vals[e] * r[i];
+    }
+    free(cols);
+    free(vals);
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (int64_t j = 0; j < N; ++j) z[j] += part[t][j];
+    free(part[t]);
+  }
+  free(part);
 }
