@@ -585,13 +585,18 @@ def main():
     # solver back projection: A^T (values + indices), column pointers, r gather,
     # the four Huber weight planes, x read and g and (p, g) written
     bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
-    # trial forward with the fused step: A (values + indices), row pointers, the
-    # (p, g) pairs read and xbar written, b read and r written; A d written in
-    # UPN trials, the four Huber weight planes in GPBB trials (weighted by the
-    # share of each method's trials among the timed launches)
+    # trial kernel: A (values + indices), row pointers, the (p, g) pairs read and
+    # xbar written, b read and r written; GP / GPBB trials write the four Huber
+    # weight planes at xbar; UPN trials read u and x and write u, A y - b, y and
+    # the planes at y (the extrapolation for the case of acceptance).  Weighted
+    # by the share of each method's trials among the timed launches.
     w_share = trials_gpbb / max(trials_gpbb + trials_upn, 1)
     bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
-                 + w_share * 16 * N + (1 - w_share) * 4 * m)
+                 + w_share * 16 * N + (1 - w_share) * (12 * m + 24 * N))
+    # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
+    t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage)
+    t_u = captured_traffic("fwd_csr_trial_upn", args.storage)
+    trial_traffic = (w_share * t_g + (1 - w_share) * t_u) if (t_g and t_u) else None
     peak, peak_kind = measured_peak_gbs()
     roof = None
     nf, msf = prof["forward"]
@@ -600,7 +605,7 @@ def main():
         ach = bytes_fwd / avg_s / 1e9
         bk = {k: 1e3 * v[1] / v[0] for k, v in breakdown.items() if v[0]}
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": captured_traffic("fwd_csr_trial", args.storage), "kernel": "fwd_csr_trial",
+                "traffic": trial_traffic, "kernel": "fwd_csr_trial",
                 "launches": nf, "avg_us": 1e6 * avg_s, "algorithmic_bytes_per_launch": bytes_fwd,
                 "peak_source": peak_kind,
                 "timing": "CUDA event nodes around the kernel in every 8th pass of the timed "

@@ -137,6 +137,29 @@ __device__ __forceinline__ void ctrl_after_grad(DevState *st, const double *tot)
   }
 }
 
+// UPN (Alg. 3) scalars that acceptance at L would give: mu_k (eq.
+// mu_k_estimate, kept non-increasing), theta_{k+1} (positive root of
+// theta^2 = (1 - theta) theta_k^2 + (mu_k / L_k) theta) and beta_k.  Used by
+// ctrl_trial and, speculatively, by the trial kernel.
+__device__ __forceinline__ double upn_next(const DevState *st, double L, double &theta_new,
+                                           double &mu_new) {
+  if (st->k == 0) {
+    mu_new = st->mubar;
+    const double q = mu_new / L;
+    theta_new = sqrt(q < 1.0 ? q : 1.0);
+    return 0.0;  // y^(1) = x^(1)
+  }
+  mu_new = st->mu;
+  if (st->M_valid) {
+    const double M = st->M > 0.0 ? st->M : 0.0;
+    mu_new = M < mu_new ? M : mu_new;
+  }
+  const double th = st->theta, q = mu_new / L;
+  const double a = th * th - q;
+  theta_new = 0.5 * (-a + sqrt(a * a + 4.0 * th * th));
+  return th * (1.0 - th) / (th * th + theta_new);
+}
+
 // Accept / reject the trial point.  r_step = {g^T d, ||d||^2, sum B_h, GPBB ||x - P(x - theta g)||^2};
 // fwd = {||A xbar - b||^2, ||A d||^2}.
 __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
@@ -201,30 +224,25 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
   st->gnorm = st->L * sqrt(dd);  // ||G_{L_k}(base)|| = L_k ||base - x+||
   if (st->k == 0) st->gnorm0 = st->gnorm;
   if (st->solver == SOLVER_UPN) {
-    double bnew;
-    if (st->k == 0) {
-      st->mu = st->mubar;
-      const double q = st->mu / st->L;
-      st->theta = sqrt(q < 1.0 ? q : 1.0);
-      bnew = 0.0;  // y^(1) = x^(1)
-    } else {
-      if (st->M_valid) {
-        const double M = st->M > 0.0 ? st->M : 0.0;
-        st->mu = M < st->mu ? M : st->mu;
-      }
-      const double th = st->theta, q = st->mu / st->L;
-      const double a = th * th - q;
-      const double tn = 0.5 * (-a + sqrt(a * a + 4.0 * th * th));
-      bnew = th * (1.0 - th) / (th * th + tn);
-      st->theta = tn;
-    }
+    double tn, mun;
+    const double bnew = upn_next(st, st->L, tn, mun);
+    st->mu = mun;
+    st->theta = tn;
     st->beta_prev = st->beta;
     st->beta = bnew;
+    if (st->spec_upn) {
+      // adopt the extrapolation the trial formed for this outcome
+      st_swap(st->vN[RN_Y], st->vN[RN_Y2]);
+      st_swap(st->vM[RM_U], st->vM[RM_U2]);
+      st_swap(st->vM[RM_RY], st->vM[RM_RY2]);
+      st_swap(st->vM[RM_RYS], st->vM[RM_RYS2]);
+      for (int i = 0; i < 3; ++i) st->r_yf[i] = st->r_spec[i];
+    }
   }
   st_swap(st->vN[RN_X], st->vN[RN_T]);
   st_swap(st->vM[RM_R], st->vM[RM_RT]);
   st_swap(st->vM[RM_RS], st->vM[RM_RTS]);
-  if (st->solver != SOLVER_UPN) st_swap(st->w, st->wt);
+  if (st->solver != SOLVER_UPN || st->spec_upn) st_swap(st->w, st->wt);
   const int tr = st->trial;
   st->trial = 0;
   st->need_grad = 1;

@@ -7,7 +7,8 @@
 //   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free) fused with
 //               the TV_tau stencil and its value; solver modes add the BB dots
 //               (GPBB) or the TV Bregman sum of the mu-estimate (UPN)
-//   k_yform     UPN extrapolation y = x+ + beta (x+ - x) and its residual A y - b
+//               (and, in UPN, the extrapolation y = x+ + beta (x+ - x) with its
+//               residual A y - b for the case of acceptance)
 //   k_tv_value  TV_tau(x) alone (phi without a gradient)
 //   k_project   P_Q in place; k_gmap gradient-map norm
 //
@@ -31,6 +32,9 @@ namespace {
 #endif
 #ifndef TVR_FWD_MIN_BLOCKS
 #define TVR_FWD_MIN_BLOCKS 5
+#endif
+#ifndef TVR_TRIAL_MIN_BLOCKS
+#define TVR_TRIAL_MIN_BLOCKS 4
 #endif
 #ifndef TVR_BWD_MIN_BLOCKS
 #define TVR_BWD_MIN_BLOCKS 5
@@ -105,7 +109,37 @@ __device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const 
   return d;
 }
 
-enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3 };
+// UPN extrapolation (Alg. 3): y = x+ + beta (x+ - x).
+__device__ __forceinline__ float y_of(float xn, float xo, float beta) {
+  return __fmaf_rn(beta, __fsub_rn(xn, xo), xn);
+}
+
+// Per-voxel part: Huber weights of D y and the Bregman term at voxel j.
+// xk / yk: x+ and y at the forward neighbours (in[e]).
+__device__ __forceinline__ void yform_voxel(float xn, float yj, const float xk[3],
+                                            const float yk[3], const bool in[3], float tau,
+                                            FF &a2, float w[3]) {
+  const float dq0 = __fsub_rn(xn, yj);
+  float z[3], zq[3], dl[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (in[e]) {
+      z[e] = __fsub_rn(yk[e], yj);
+      zq[e] = __fsub_rn(xk[e], xn);
+      dl[e] = __fsub_rn(__fsub_rn(xk[e], yk[e]), dq0);
+    } else {
+      z[e] = zq[e] = dl[e] = 0.f;
+    }
+  }
+  const float nz = norm3(z);
+  huber_weights(z, nz, tau, w);
+  ff_add(a2, huber_bregman(z, nz, zq, dl, tau));
+}
+
+// FWD_TRIAL_X: the UPN trial, which also forms the extrapolation for the
+// case of acceptance (a separate instance, so that the GP / GPBB trial keeps
+// its register budget).
+enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3, FWD_TRIAL_X = 4 };
 enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP = 4 };
 
 // ---------------------------------------------------------------------------
@@ -113,40 +147,58 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool BF, bool MF = false>
-__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR_TRIAL_MIN_BLOCKS
+                                                                            : TVR_FWD_MIN_BLOCKS))
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
               float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1,
               float *__restrict__ rsout = nullptr) {
+  constexpr bool TRIAL = MODE == FWD_TRIAL || MODE == FWD_TRIAL_X;
+  constexpr bool SPEC = MODE == FWD_TRIAL_X;
   pdl_enter();
   const float *x = xin;
   const float2 *pg = nullptr;  // trial mode: (p_j, g_j) per voxel
   float s = 0.f;               // trial mode: step size
   float *r = rout;
   float *rs = rsout;           // BF16 storage: r times the row scale
-  float *ad = nullptr;
+  // UPN: the extrapolation for the case of acceptance (see DevState::spec_upn)
+  const float *u_old = nullptr;
+  float *u2 = nullptr, *ry2 = nullptr, *rys2 = nullptr;
+  float bcur = 0.f, bnew = 0.f;
   if (MODE == FWD_INIT) {
     const bool upn = st->solver == SOLVER_UPN;
     b = st->b;
     x = upn ? st->vN[RN_Y] : st->vN[RN_X];
     r = upn ? st->vM[RM_RY] : st->vM[RM_R];
     rs = upn ? st->vM[RM_RYS] : st->vM[RM_RS];
-  } else if (MODE == FWD_TRIAL) {
+  } else if (TRIAL) {
     if (st->done) return;
     if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->prof_flags[prof_slot] = 1;
-    const bool upn = st->solver == SOLVER_UPN;
     b = st->b;
     pg = st->pg;
     s = (float)st->step;
     r = st->vM[RM_RT];
     rs = st->vM[RM_RTS];
-    ad = upn ? st->vM[RM_AD] : nullptr;
+    if (SPEC) {
+      __shared__ float sh_bnew;
+      u_old = st->vM[RM_U];
+      u2 = st->vM[RM_U2];
+      ry2 = st->vM[RM_RY2];
+      rys2 = BF ? st->vM[RM_RYS2] : nullptr;
+      bcur = (float)st->beta;  // beta_{k-1}: u = A(x+ - y) + beta_{k-1} u_{k-1}
+      if (threadIdx.x == 0) {
+        double tn, mun;
+        sh_bnew = (float)upn_next(st, st->Lt, tn, mun);  // beta_k if this trial is accepted
+      }
+      __syncthreads();
+      bnew = sh_bnew;
+    }
   }
   constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & (G - 1);
   const int sub = (threadIdx.x & 31) / G;
   const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
   const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
-  FF a0 = ff_zero(), a1 = ff_zero();
+  FF a0 = ff_zero(), a1 = ff_zero(), au = ff_zero();
   for (int64_t base = warp * RPW; base < A.m; base += nwarp * RPW) {
     const int64_t row = base + sub;
     const bool valid = row < A.m;
@@ -165,7 +217,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
       MfRay ray;
       mf_pixel_ray(A.mfv[vi], A.kind, A.Pu, A.Pv, pp, q, ray);
       mf_row<G>(ray, A.n, lane, [&](int c, float v) {
-        if (MODE == FWD_TRIAL) {
+        if (TRIAL) {
           const float2 qc = __ldg(pg + c);
           const float bc = xbar_of(qc.x, qc.y, s);
           sx = __fmaf_rn(v, bc, sx);
@@ -196,7 +248,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
 #pragma unroll
       for (int u = 0; u < kRowChunks; ++u) {
         if (e0 + (int64_t)u * 4 * G >= end) break;
-        if (MODE == FWD_TRIAL) {
+        if (TRIAL) {
           // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
           const float2 q0 = __ldg(pg + c4[u].x), q1 = __ldg(pg + c4[u].y);
           const float2 q2 = __ldg(pg + c4[u].z), q3 = __ldg(pg + c4[u].w);
@@ -221,7 +273,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
       }
     }
     sx = group_sum<G>(sx);
-    if (MODE == FWD_TRIAL) sd = group_sum<G>(sd);
+    if (TRIAL) sd = group_sum<G>(sd);
     if (valid && lane == 0) {
       float sc = 1.f;
       if (BF) {
@@ -236,15 +288,22 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
         r[row] = ri;
         if (BF && rs) rs[row] = __fmul_rn(sc, ri);
         ff_add_prod(a0, ri, ri);
-        if (MODE == FWD_TRIAL) {
-          if (ad) ad[row] = sd;
+        if (TRIAL) {
           ff_add_prod(a1, sd, sd);
+          if (SPEC) {  // UPN: u and A y - b for the case of acceptance (residual by linearity)
+            const float un = __fmaf_rn(bcur, u_old[row], sd);
+            u2[row] = un;
+            const float ry = __fmaf_rn(bnew, un, ri);
+            ry2[row] = ry;
+            if (BF && rys2) rys2[row] = __fmul_rn(sc, ry);
+            ff_add_prod(au, un, un);
+          }
         }
       }
     }
   }
   if (MODE == FWD_Y) return;
-  if (MODE != FWD_TRIAL) {
+  if (!TRIAL) {
     FF acc[1] = {a0};
     double tot[1];
     if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0 && MODE == FWD_INIT)
@@ -256,14 +315,20 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
   // forward neighbours is recomputed with the same expression, so the TV
   // Bregman sum and the Huber weights (written for GP / GPBB, whose next
   // gradient is taken at the accepted xbar) see exactly the stored values.
-  FF s0 = ff_zero(), s1 = ff_zero(), s2 = ff_zero(), s3 = ff_zero();
+  // UPN: also y = x+ + beta_k (x+ - x) for the case of acceptance, the
+  // Huber weights of D y, ||x+ - x||^2 and sum_j B_h(D_j x+; D_j y) (Alg. 3,
+  // eq. mu_k_estimate), recomputing y at the forward neighbours.
+  FF s0 = ff_zero(), s1 = ff_zero(), s2 = ff_zero(), s3 = ff_zero(), sb = ff_zero();
   {
     const bool upn = st->solver == SOLVER_UPN;
+    constexpr bool spec = SPEC;
     const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
     const float sg2 = (float)st->step2;
     const float tau = (float)st->tau;
     float *__restrict__ t = st->vN[RN_T];
-    float *__restrict__ wt = upn ? nullptr : st->wt;
+    float *__restrict__ wt = (!upn || spec) ? st->wt : nullptr;
+    const float *__restrict__ xo = st->vN[RN_X];
+    float *__restrict__ y2 = st->vN[RN_Y2];
     const int n = A.n;
     const int64_t nn = (int64_t)n * n, N = A.N;
     const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
@@ -284,7 +349,18 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
       float w[3];
       step_voxel(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, w);
       t[j] = xb;
-      if (wt) {
+      if (spec) {
+        const float xoj = xo[j];
+        const float dx = __fsub_rn(xb, xoj);
+        const float yj = __fmaf_rn(bnew, dx, xb);
+        ff_add_prod(s3, dx, dx);
+        float yk[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) yk[e] = in[e] ? y_of(xk[e], xo[j + off[e]], bnew) : 0.f;
+        yform_voxel(xb, yj, xk, yk, in, tau, sb, w);
+        y2[j] = yj;
+      }
+      if (wt) {  // Huber weights at the next gradient point: xbar (GP, GPBB) or y (UPN)
         wt[j] = w[0];
         wt[N + j] = w[1];
         wt[2 * N + j] = w[2];
@@ -292,13 +368,19 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_FWD_MIN_BLOCKS)
       }
     }
   }
-  FF acc[6] = {a0, a1, s0, s1, s2, s3};
-  double tot[6];
-  if (grid_reduce<6>(acc, slot, tot) && threadIdx.x == 0) {
+  // slot 5: GPBB ||x - P(x - theta g)||^2, or UPN ||x+ - x||^2
+  FF acc[8] = {a0, a1, s0, s1, s2, s3, au, sb};
+  double tot[8];
+  if (grid_reduce<8>(acc, slot, tot) && threadIdx.x == 0) {
     st->r_fwd[0] = tot[0];
     st->r_fwd[1] = tot[1];
 #pragma unroll
     for (int k = 0; k < 4; ++k) st->r_step[k] = tot[2 + k];
+    if (SPEC) {
+      st->r_spec[0] = tot[5];
+      st->r_spec[1] = tot[6];
+      st->r_spec[2] = tot[7];
+    }
     ctrl_trial(st, tot);
   }
 }
@@ -476,106 +558,6 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
   }
 }
 
-// ---------------------------------------------------------------------------
-// UPN extrapolation (Alg. 3): y = x+ + beta (x+ - x) and, by linearity of A,
-//   u  = A(x+ - x) = A(x+ - y_prev) + beta_prev u_prev,
-//   A y - b = (A x+ - b) + beta u,
-// so the residual at y needs no projection.  The kernel also writes the Huber
-// weights of D y (the TV part of the gradient at y) and sums the TV Bregman
-// term sum_j B_h(D_j x+; D_j y) of the mu-estimate, recomputing y at the
-// forward neighbours with the same expression.  Reductions: ||x+ - x||^2,
-// ||u||^2, sum_j B_h.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float y_of(float xn, float xo, float beta) {
-  return __fmaf_rn(beta, __fsub_rn(xn, xo), xn);
-}
-
-// Per-voxel part: Huber weights of D y and the Bregman term at voxel j.
-// xk / yk: x+ and y at the forward neighbours (in[e]).
-__device__ __forceinline__ void yform_voxel(float xn, float yj, const float xk[3],
-                                            const float yk[3], const bool in[3], float tau,
-                                            FF &a2, float w[3]) {
-  const float dq0 = __fsub_rn(xn, yj);
-  float z[3], zq[3], dl[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    if (in[e]) {
-      z[e] = __fsub_rn(yk[e], yj);
-      zq[e] = __fsub_rn(xk[e], xn);
-      dl[e] = __fsub_rn(__fsub_rn(xk[e], yk[e]), dq0);
-    } else {
-      z[e] = zq[e] = dl[e] = 0.f;
-    }
-  }
-  const float nz = norm3(z);
-  huber_weights(z, nz, tau, w);
-  ff_add(a2, huber_bregman(z, nz, zq, dl, tau));
-}
-
-__global__ void __launch_bounds__(TVR_BLOCK, 4)
-    k_yform(MatDev A, RedSlot slot, DevState *st, int prof_slot) {
-  pdl_enter();
-  if (st->done || !st->need_grad) return;
-  if (prof_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
-    st->prof_flags[3 * TVR_PROF_PAIRS + prof_slot] = 1;
-  const float beta = (float)st->beta, bp = (float)st->beta_prev;
-  const float *__restrict__ X = st->vN[RN_X];
-  const float *__restrict__ T = st->vN[RN_T];
-  float *__restrict__ Y = st->vN[RN_Y];
-  const float *__restrict__ R = st->vM[RM_R];
-  const float *__restrict__ AD = st->vM[RM_AD];
-  float *__restrict__ U = st->vM[RM_U];
-  float *__restrict__ RY = st->vM[RM_RY];
-  float *__restrict__ RYS = A.bf16 ? st->vM[RM_RYS] : nullptr;
-  float *__restrict__ W = st->w;
-  const float tau = (float)st->tau;
-  const int n = A.n;
-  const int64_t N = A.N, m = A.m;
-  const int64_t nn = (int64_t)n * n;
-  FF a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
-  const int64_t tid = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
-    for (int64_t i = tid; i < N; i += stride) {
-      const float xn = X[i];
-      const float dx = __fsub_rn(xn, T[i]);
-      const float yj = __fmaf_rn(beta, dx, xn);
-      Y[i] = yj;
-      ff_add_prod(a0, dx, dx);
-      int ix, iy, iz;
-      voxel_of(A, i, ix, iy, iz);
-      const int64_t off[3] = {1, n, nn};
-      const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
-      float xk[3], yk[3];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        xk[e] = in[e] ? X[i + off[e]] : 0.f;
-        yk[e] = in[e] ? y_of(xk[e], T[i + off[e]], beta) : 0.f;
-      }
-      float w[3];
-      yform_voxel(xn, yj, xk, yk, in, tau, a2, w);
-      W[i] = w[0];
-      W[N + i] = w[1];
-      W[2 * N + i] = w[2];
-      W[3 * N + i] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
-  }
-  // residual at y by linearity (rows)
-  for (int64_t i = tid; i < m; i += stride) {
-    const float u = __fmaf_rn(bp, U[i], AD[i]);
-    U[i] = u;
-    const float ry = __fmaf_rn(beta, u, R[i]);
-    RY[i] = ry;
-    if (RYS) RYS[i] = __fmul_rn(A.rscale[i], ry);
-    ff_add_prod(a1, u, u);
-  }
-  FF acc[3] = {a0, a1, a2};
-  double tot[3];
-  if (grid_reduce<3>(acc, slot, tot) && threadIdx.x == 0) {
-    st->r_yf[0] = tot[0];
-    st->r_yf[1] = tot[1];
-    st->r_yf[2] = tot[2];
-  }
-}
-
 // TV_tau(x) alone; finishes phi from the forward kernel's 1/2||r||^2.
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_tv_value(MatDev A, const float *__restrict__ x, float tau, double alpha_d, RedSlot slot,
@@ -646,9 +628,11 @@ int occupancy_grid(const void *kernel, int block, int device) {
 void kernel_grids(Workspace &ws, int device) {
   ws.grid_fwd =
       occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device);
+  ws.grid_trial_x =
+      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_X, false>, TVR_BLOCK, device);
   ws.grid_bwd =
       occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device);
-  ws.grid_elem = occupancy_grid((const void *)k_yform, TVR_BLOCK, device);
+  ws.grid_elem = occupancy_grid((const void *)k_tv_value, TVR_BLOCK, device);
 }
 
 // Launch with programmatic stream serialization (the kernel calls pdl_enter
@@ -731,8 +715,9 @@ void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cuda
              ws.bwd, nullptr, nullptr, st, -1, nullptr, nullptr);
 }
 
-// One pass: [UPN: extrapolation] -> gradient at the new point (skipped after a
-// rejected trial) -> projected trial step -> forward projection + test.
+// One pass: gradient at the new point (skipped after a rejected trial) ->
+// trial kernel (forward projection with the projected step fused, UPN's
+// extrapolation for the case of acceptance, the acceptance test).
 void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
                         cudaStream_t s, const PassTiming *tm) {
   auto mark = [&](int kind, int which) {
@@ -743,17 +728,13 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
       cudaEventRecord(tm->ev[kind][which], s);
   };
   auto slot = [&](int kind) { return tm ? tm->slot[kind] : -1; };
-  if (solver == SOLVER_UPN) {
-    mark(3, 0);
-    launch_pdl(k_yform, elem_grid(A.N > A.m ? A.N : A.m, ws.grid_elem), s, A, ws.yf, st, slot(3));
-    mark(3, 1);
-  }
   mark(1, 0);
   launch_pdl(bwd_kernel<BWD_SOLVER>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
              ws.bwd, nullptr, nullptr, st, slot(1), nullptr, nullptr);
   mark(1, 1);
   mark(0, 0);
-  launch_pdl(fwd_kernel<FWD_TRIAL>(A), ws.grid_fwd, s, A, nullptr, nullptr, nullptr, ws.fwd, st,
-             slot(0), nullptr);
+  launch_pdl(solver == SOLVER_UPN ? fwd_kernel<FWD_TRIAL_X>(A) : fwd_kernel<FWD_TRIAL>(A),
+             solver == SOLVER_UPN ? ws.grid_trial_x : ws.grid_fwd, s, A, nullptr, nullptr, nullptr,
+             ws.fwd, st, slot(0), nullptr);
   mark(0, 1);
 }

@@ -42,9 +42,12 @@ int ensure_solver(tvr_system *sys, int64_t hist_records) {
   return TVR_OK;
 }
 
-// Kernel kinds a solver pass launches: forward (with the fused step), back
-// projection, and the extrapolation in UPN.
-bool pass_kind(int k, int solver) { return k == 0 || k == 1 || (k == 3 && solver == SOLVER_UPN); }
+// Kernel kinds a solver pass launches: back projection and the trial kernel
+// (forward projection with the step and UPN's extrapolation fused).
+bool pass_kind(int k, int solver) {
+  (void)solver;
+  return k == 0 || k == 1;
+}
 
 // A batch of passes captured once per (system, method, batch size) and
 // replayed.  With kernel timing on, the graph also holds an event node pair
@@ -185,9 +188,9 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   const cudaMemcpyKind kin = j.xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   TVR_CUDA(cudaMemcpyAsync(sys->vN[0], x, sizeof(float) * sys->N, kin, s));
   if (solver == SOLVER_UPN) {
-    TVR_CUDA(cudaMemcpyAsync(sys->vN[2], sys->vN[0], sizeof(float) * sys->N,
+    TVR_CUDA(cudaMemcpyAsync(sys->vN[RN_Y], sys->vN[RN_X], sizeof(float) * sys->N,
                              cudaMemcpyDeviceToDevice, s));
-    TVR_CUDA(cudaMemsetAsync(sys->vM[3], 0, sizeof(float) * sys->m, s));
+    TVR_CUDA(cudaMemsetAsync(sys->vM[RM_U], 0, sizeof(float) * sys->m, s));
   }
   DevState h;
   std::memset(&h, 0, sizeof(h));
@@ -205,6 +208,7 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   h.bt_max = o.bt_max;
   h.stop_mode = o.stop_mode;
   h.solver = solver;
+  h.spec_upn = solver == SOLVER_UPN;
   h.N = sys->N;
   h.b = j.bd;
   for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];

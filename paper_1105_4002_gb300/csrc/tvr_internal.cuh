@@ -283,11 +283,15 @@ __device__ __forceinline__ float huber_bregman(const float z[3], float nz, const
 // ---------------------------------------------------------------------------
 enum SolverKind { SOLVER_NONE = 0, SOLVER_GP = 1, SOLVER_GPBB = 2, SOLVER_UPN = 3 };
 
-enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_COUNT };
+// Y2, RY2, U2, RYS2: UPN's extrapolation formed speculatively by each trial
+// (the values y, A y - b, u would take if the trial is accepted); they swap
+// with Y, RY, U, RYS on acceptance.
+enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_Y2, RN_COUNT };
 // RS, RTS, RYS: the residuals R, RT, RY times the per-row scales (BF16 storage
 // only), which the back projection gathers so that it applies the same
 // matrix s_i q_ij as the forward projection.
-enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_RS, RM_RTS, RM_RYS, RM_COUNT };
+enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_RY2, RM_U2, RM_RS, RM_RTS, RM_RYS, RM_RYS2,
+             RM_COUNT };
 
 #define TVR_FHIST 16
 
@@ -308,6 +312,13 @@ struct DevState {
   int total_trials, f_evals, g_evals;
   // reduction results
   double r_init[TVR_RMAX], r_fwd[TVR_RMAX], r_bwd[TVR_RMAX], r_step[TVR_RMAX], r_yf[TVR_RMAX];
+  // UPN with the extrapolation fused into the trial kernel: the trial also
+  // forms y, u, A y - b and the Huber weights of y for the case of acceptance
+  // (roles Y2, U2, RY2, RYS2 and the planes wt) with the reductions r_spec =
+  // {||x+ - x||^2, ||u||^2, sum_j B_h(D_j x+; D_j y)}; ctrl_trial adopts them
+  // on acceptance.
+  int spec_upn;
+  double r_spec[3];
   // vector roles
   float *vN[RN_COUNT];
   float *vM[RM_COUNT];
@@ -398,7 +409,7 @@ __device__ __forceinline__ void voxel_of(const MatDev &A, int64_t j, int &ix, in
 
 struct Workspace {
   RedSlot fwd, bwd, step, yf, tv, gmap;
-  int grid_fwd, grid_bwd, grid_elem;
+  int grid_fwd, grid_bwd, grid_elem, grid_trial_x;
 };
 
 // Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from
