@@ -19,10 +19,16 @@ roofline = the dominant kernel (CSC back projection + TV, or CSR forward
 """
 from __future__ import annotations
 
+import os
+
+# The CPU legs (the oracle) run on one host thread: numpy's BLAS would
+# otherwise spread vector products over all cores.  Set before numpy loads.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
 import math
-import os
 import subprocess
 import sys
 import threading
@@ -143,6 +149,19 @@ def captured_traffic(kernel: str, storage: str = "fp32"):
         return rec.get(kernel)
     except Exception:
         return None
+
+
+def aggregate(dist, count: float, ms: float, device):
+    """Whole-job figures over the ranks: (sum of the work counts, max of the
+    times).  dist is torch.distributed (any backend) or None for one process."""
+    if dist is None:
+        return float(count), float(ms)
+    import torch
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(c.item()), float(t.item())
 
 
 def gpu_id_for(torch, dev):
@@ -518,15 +537,7 @@ def main():
     breakdown = sysm.profile_read()
     sysm.profile(False)
 
-    tot = torch.tensor([float(evals), elapsed_ms], dtype=torch.float64, device=dev)
-    if dist:
-        ev_t = tot[:1].clone()
-        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
-        t_t = tot[1:].clone()
-        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
-        evals_all, elapsed_max = float(ev_t.item()), float(t_t.item())
-    else:
-        evals_all, elapsed_max = float(evals), elapsed_ms
+    evals_all, elapsed_max = aggregate(dist, evals, elapsed_ms, dev)
     value = evals_all / (elapsed_max / 1e3)
 
     # ---- end-to-end through the public call with host buffers ----
@@ -542,14 +553,8 @@ def main():
         r2 = sysm.solve("upn", b_pin, cfg.alpha, cfg.tau, eps, xu_h.zero_(), opts)
         e_evals += r1.g_evals + r2.g_evals
     e_ms = 1e3 * (time.perf_counter() - t0)
-    e2e_value = e_evals / (e_ms / 1e3)
-    if dist:
-        tt = torch.tensor([float(e_evals), e_ms], dtype=torch.float64, device=dev)
-        a = tt[:1].clone()
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        m_ = tt[1:].clone()
-        dist.all_reduce(m_, op=dist.ReduceOp.MAX)
-        e2e_value = float(a.item()) / (float(m_.item()) / 1e3)
+    e_all, e_max = aggregate(dist, e_evals, e_ms, dev)
+    e2e_value = e_all / (e_max / 1e3)
 
     # ---- standalone phi_and_grad rate (same kernels, plain mode) ----
     xr = torch.tensor(np.random.default_rng(rank).uniform(0, 1, geom.N), dtype=torch.float32,

@@ -79,8 +79,9 @@ __device__ __forceinline__ float xbar_of(float p, float g, float s) {
 }
 
 // Per-voxel part of the step: d = xbar_j - p_j, the terms of g^T d, ||d||^2,
-// the GPBB ||x - P(x - theta g)||^2 and the TV Bregman sum, and the Huber
+// the GPBB ||x - P(x - theta g)||^2 and the TV Bregman sum, and (W) the Huber
 // weights at xbar.  pk / xk: p and xbar at the forward neighbours (in[e]).
+template <bool W = true>
 __device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const float pk[3],
                                             const float xk[3], const bool in[3], float s2,
                                             bool want_g2, float tau, FF &a0, FF &a1, FF &a2,
@@ -105,7 +106,7 @@ __device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const 
   }
   const float nb = norm3(zb);
   ff_add(a2, huber_bregman_n(z, norm3(z), zb, nb, dl, tau));
-  huber_weights(zb, nb, tau, w);
+  if (W) huber_weights(zb, nb, tau, w);
   return d;
 }
 
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
       }
       float w[3];
-      step_voxel(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, w);
+      step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, w);
       t[j] = xb;
       if (spec) {
         const float xoj = xo[j];
