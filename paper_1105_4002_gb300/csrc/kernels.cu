@@ -39,14 +39,6 @@ namespace {
 #ifndef TVR_BWD_MIN_BLOCKS
 #define TVR_BWD_MIN_BLOCKS 5
 #endif
-#ifndef TVR_ROW_CHUNKS
-#define TVR_ROW_CHUNKS 2
-#endif
-#ifndef TVR_COL_CHUNKS
-#define TVR_COL_CHUNKS 2
-#endif
-constexpr int kRowChunks = TVR_ROW_CHUNKS;  // 4-entry chunks per lane per loop trip (CSR)
-constexpr int kColChunks = TVR_COL_CHUNKS;  // same for the CSC loop
 constexpr int kRowLanes = TVR_ROW_LANES;  // lanes per CSR row
 constexpr int kColLanes = TVR_COL_LANES;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
 static_assert(kColLanes >= 4 && kColLanes <= 32 && (kColLanes & (kColLanes - 1)) == 0, "lanes");
@@ -229,48 +221,49 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
       });
     }
     // Rows are padded to multiples of 4 entries: each lane reads 4 entries
-    // with one 16-byte load of indices and one of values, then gathers.
-    // Trial mode gathers (xbar_j, xbar_j - p_j) pairs with one 8-byte load.
-    for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kRowChunks) {
-      // all index / value loads of this trip first, then the gathers
-      int4 c4[kRowChunks];
-      float4 v4[kRowChunks];
-#pragma unroll
-      for (int u = 0; u < kRowChunks; ++u) {
-        const int64_t e = e0 + (int64_t)u * 4 * G;
-        if (e < end) {
-          c4[u] = __ldg(reinterpret_cast<const int4 *>(A.col + e));
-          v4[u] = load4<BF>(A.val, A.qval, e);
-        } else {
-          c4[u] = make_int4(0, 0, 0, 0);
-          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // with one 16-byte load of indices and one of values, then gathers.  The
+    // loads of the lane's next 4 entries are issued before this trip's
+    // arithmetic waits on its gathers (a two-stage software pipeline).
+    int64_t e0 = beg + 4 * lane;
+    int4 cn = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e0 < end) {
+      cn = __ldg(reinterpret_cast<const int4 *>(A.col + e0));
+      vn = load4<BF>(A.val, A.qval, e0);
+    }
+    for (; e0 < end; e0 += 4 * G) {
+      const int4 c4 = cn;
+      const float4 v4 = vn;
+      const int64_t e1 = e0 + 4 * G;
+      if (TRIAL) {
+        // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
+        const float2 q0 = __ldg(pg + c4.x), q1 = __ldg(pg + c4.y);
+        const float2 q2 = __ldg(pg + c4.z), q3 = __ldg(pg + c4.w);
+        if (e1 < end) {
+          cn = __ldg(reinterpret_cast<const int4 *>(A.col + e1));
+          vn = load4<BF>(A.val, A.qval, e1);
         }
-      }
-#pragma unroll
-      for (int u = 0; u < kRowChunks; ++u) {
-        if (e0 + (int64_t)u * 4 * G >= end) break;
-        if (TRIAL) {
-          // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
-          const float2 q0 = __ldg(pg + c4[u].x), q1 = __ldg(pg + c4[u].y);
-          const float2 q2 = __ldg(pg + c4[u].z), q3 = __ldg(pg + c4[u].w);
-          const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
-          const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
-          sx = __fmaf_rn(v4[u].x, b0, sx);
-          sd = __fmaf_rn(v4[u].x, __fsub_rn(b0, q0.x), sd);
-          sx = __fmaf_rn(v4[u].y, b1, sx);
-          sd = __fmaf_rn(v4[u].y, __fsub_rn(b1, q1.x), sd);
-          sx = __fmaf_rn(v4[u].z, b2, sx);
-          sd = __fmaf_rn(v4[u].z, __fsub_rn(b2, q2.x), sd);
-          sx = __fmaf_rn(v4[u].w, b3, sx);
-          sd = __fmaf_rn(v4[u].w, __fsub_rn(b3, q3.x), sd);
-        } else {
-          const float x0 = __ldg(x + c4[u].x), x1 = __ldg(x + c4[u].y);
-          const float x2 = __ldg(x + c4[u].z), x3 = __ldg(x + c4[u].w);
-          sx = __fmaf_rn(v4[u].x, x0, sx);
-          sx = __fmaf_rn(v4[u].y, x1, sx);
-          sx = __fmaf_rn(v4[u].z, x2, sx);
-          sx = __fmaf_rn(v4[u].w, x3, sx);
+        const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
+        const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
+        sx = __fmaf_rn(v4.x, b0, sx);
+        sd = __fmaf_rn(v4.x, __fsub_rn(b0, q0.x), sd);
+        sx = __fmaf_rn(v4.y, b1, sx);
+        sd = __fmaf_rn(v4.y, __fsub_rn(b1, q1.x), sd);
+        sx = __fmaf_rn(v4.z, b2, sx);
+        sd = __fmaf_rn(v4.z, __fsub_rn(b2, q2.x), sd);
+        sx = __fmaf_rn(v4.w, b3, sx);
+        sd = __fmaf_rn(v4.w, __fsub_rn(b3, q3.x), sd);
+      } else {
+        const float x0 = __ldg(x + c4.x), x1 = __ldg(x + c4.y);
+        const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
+        if (e1 < end) {
+          cn = __ldg(reinterpret_cast<const int4 *>(A.col + e1));
+          vn = load4<BF>(A.val, A.qval, e1);
         }
+        sx = __fmaf_rn(v4.x, x0, sx);
+        sx = __fmaf_rn(v4.y, x1, sx);
+        sx = __fmaf_rn(v4.z, x2, sx);
+        sx = __fmaf_rn(v4.w, x3, sx);
       }
     }
     sx = group_sum<G>(sx);
@@ -466,36 +459,35 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
       mf_column<G>(A.mfv, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
                    [&](int64_t i, float v) { s = __fmaf_rn(v, __ldg(r + i), s); });
     }
-    for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G * kColChunks) {
-      int4 i4[kColChunks];
-      float4 v4[kColChunks];
-#pragma unroll
-      for (int u = 0; u < kColChunks; ++u) {
-        const int64_t e = e0 + (int64_t)u * 4 * G;
-        if (e < end) {
-          i4[u] = __ldg(reinterpret_cast<const int4 *>(A.row + e));
-          v4[u] = load4<BF>(A.cval, A.qcval, e);
-        } else {
-          i4[u] = make_int4(0, 0, 0, 0);
-          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+    // two-stage software pipeline over the lane's 4-entry groups, as in the
+    // forward projection
+    int64_t e0 = beg + 4 * lane;
+    int4 in4 = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e0 < end) {
+      in4 = __ldg(reinterpret_cast<const int4 *>(A.row + e0));
+      vn = load4<BF>(A.cval, A.qcval, e0);
+    }
+    for (; e0 < end; e0 += 4 * G) {
+      const int4 i4 = in4;
+      const float4 v4 = vn;
+      float r0 = __ldg(r + i4.x), r1 = __ldg(r + i4.y);
+      float r2 = __ldg(r + i4.z), r3 = __ldg(r + i4.w);
+      const int64_t e1 = e0 + 4 * G;
+      if (e1 < end) {
+        in4 = __ldg(reinterpret_cast<const int4 *>(A.row + e1));
+        vn = load4<BF>(A.cval, A.qcval, e1);
       }
-#pragma unroll
-      for (int u = 0; u < kColChunks; ++u) {
-        if (e0 + (int64_t)u * 4 * G >= end) break;
-        float r0 = __ldg(r + i4[u].x), r1 = __ldg(r + i4[u].y);
-        float r2 = __ldg(r + i4[u].z), r3 = __ldg(r + i4[u].w);
-        if (BF && (MODE == BWD_ADJ || MODE == BWD_VJP)) {  // caller's r: apply the row scales
-          r0 = __fmul_rn(r0, __ldg(A.rscale + i4[u].x));
-          r1 = __fmul_rn(r1, __ldg(A.rscale + i4[u].y));
-          r2 = __fmul_rn(r2, __ldg(A.rscale + i4[u].z));
-          r3 = __fmul_rn(r3, __ldg(A.rscale + i4[u].w));
-        }
-        s = __fmaf_rn(v4[u].x, r0, s);
-        s = __fmaf_rn(v4[u].y, r1, s);
-        s = __fmaf_rn(v4[u].z, r2, s);
-        s = __fmaf_rn(v4[u].w, r3, s);
+      if (BF && (MODE == BWD_ADJ || MODE == BWD_VJP)) {  // caller's r: apply the row scales
+        r0 = __fmul_rn(r0, __ldg(A.rscale + i4.x));
+        r1 = __fmul_rn(r1, __ldg(A.rscale + i4.y));
+        r2 = __fmul_rn(r2, __ldg(A.rscale + i4.z));
+        r3 = __fmul_rn(r3, __ldg(A.rscale + i4.w));
       }
+      s = __fmaf_rn(v4.x, r0, s);
+      s = __fmaf_rn(v4.y, r1, s);
+      s = __fmaf_rn(v4.z, r2, s);
+      s = __fmaf_rn(v4.w, r3, s);
     }
     s = group_sum<G>(s);
     if (MODE == BWD_ADJ) {
