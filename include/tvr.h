@@ -213,7 +213,10 @@ typedef enum tvr_stop_mode {
   TVR_STOP_PER_N = 1  /* ||G_k|| / N <= eps, as printed in the paper */
 } tvr_stop_mode;
 
-/* Number of doubles per history record: k, ||G||, L or theta, mu, beta, trials, f, stop value. */
+/* Number of doubles per history record: k, ||G||, L or theta, mu, beta, trials, f, stop value.
+   f = phi(x^(k+1)): GPBB keeps it as phi(x^(0)) plus the exact increments of the
+   accepted steps; GP and UPN evaluate it from the accepted trial's residual and
+   TV sums. */
 #define TVR_HIST_FIELDS 8
 
 typedef struct tvr_solve_opts {

@@ -202,8 +202,11 @@ class System:
 
     # ---- solvers ----
     def solve(self, method: str, b, alpha: float, tau: float, eps: float, x,
-              opts: SolveOptions | None = None, stream=None) -> SolveResult:
-        """Run GP / GPBB / UPN from x (x0 in, x* out)."""
+              opts: SolveOptions | None = None, stream=None,
+              raise_on_error: bool = True) -> SolveResult:
+        """Run GP / GPBB / UPN from x (x0 in, x* out: the last accepted iterate).
+        With raise_on_error=False a line-search or non-finite stop is returned
+        in the result's status instead of raised."""
         fn = {"gp": lib().tvr_solve_gp, "gpbb": lib().tvr_solve_gpbb,
               "upn": lib().tvr_solve_upn}[method]
         o = opts or SolveOptions()
@@ -223,7 +226,8 @@ class System:
         info = _capi.SolveInfo()
         st = fn(self._h, pb, float(alpha), float(tau), float(eps), ctypes.byref(co), px,
                 ctypes.byref(info), _stream(stream, b, x))
-        check(st, f"tvr_solve_{method}", allow=(TVR_OK, TVR_NOT_CONVERGED))
+        if raise_on_error or st not in (_capi.TVR_ERR_LINESEARCH, _capi.TVR_ERR_NONFINITE):
+            check(st, f"tvr_solve_{method}", allow=(TVR_OK, TVR_NOT_CONVERGED))
         return SolveResult(status=info.status, iters=info.iters, f_evals=info.f_evals,
                            g_evals=info.g_evals, trials=info.trials, passes=info.passes,
                            phi=info.phi, gnorm=info.gnorm, gnorm0=info.gnorm0,

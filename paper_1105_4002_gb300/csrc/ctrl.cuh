@@ -221,6 +221,7 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
     return;
   }
   st->L = st->Lt;
+  st->f_cur = 0.5 * fwd[0] + st->alpha * st->r_step[4];  // phi(x+) of the accepted trial
   st->gnorm = st->L * sqrt(dd);  // ||G_{L_k}(base)|| = L_k ||base - x+||
   if (st->k == 0) st->gnorm0 = st->gnorm;
   if (st->solver == SOLVER_UPN) {
@@ -250,5 +251,5 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
   st->step = 1.0 / st->Lt;
   st_stop_test(st);
   st_hist(st, st->k - 1, st->gnorm, st->L, st->solver == SOLVER_UPN ? st->mu : 0.0,
-          st->solver == SOLVER_UPN ? st->beta : 0.0, tr, NAN, st->stopval);
+          st->solver == SOLVER_UPN ? st->beta : 0.0, tr, st->f_cur, st->stopval);
 }

@@ -71,13 +71,14 @@ __device__ __forceinline__ float xbar_of(float p, float g, float s) {
 }
 
 // Per-voxel part of the step: d = xbar_j - p_j, the terms of g^T d, ||d||^2,
-// the GPBB ||x - P(x - theta g)||^2 and the TV Bregman sum, and (W) the Huber
-// weights at xbar.  pk / xk: p and xbar at the forward neighbours (in[e]).
+// the GPBB ||x - P(x - theta g)||^2, the TV Bregman sum and h_tau(D_j xbar)
+// (for phi(xbar)), and (W) the Huber weights at xbar.  pk / xk: p and xbar at
+// the forward neighbours (in[e]).
 template <bool W = true>
 __device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const float pk[3],
                                             const float xk[3], const bool in[3], float s2,
                                             bool want_g2, float tau, FF &a0, FF &a1, FF &a2,
-                                            FF &a3, float w[3]) {
+                                            FF &a3, FF &ah, float w[3]) {
   const float d = __fsub_rn(xb, pj);
   ff_add_prod(a0, gj, d);
   ff_add_prod(a1, d, d);
@@ -98,6 +99,7 @@ __device__ __forceinline__ float step_voxel(float pj, float gj, float xb, const 
   }
   const float nb = norm3(zb);
   ff_add(a2, huber_bregman_n(z, norm3(z), zb, nb, dl, tau));
+  ff_add(ah, huber_h(nb, tau));
   if (W) huber_weights(zb, nb, tau, w);
   return d;
 }
@@ -313,6 +315,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
   // Huber weights of D y, ||x+ - x||^2 and sum_j B_h(D_j x+; D_j y) (Alg. 3,
   // eq. mu_k_estimate), recomputing y at the forward neighbours.
   FF s0 = ff_zero(), s1 = ff_zero(), s2 = ff_zero(), s3 = ff_zero(), sb = ff_zero();
+  FF sh = ff_zero();  // TV_tau(xbar)
   {
     const bool upn = st->solver == SOLVER_UPN;
     constexpr bool spec = SPEC;
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
       }
       float w[3];
-      step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, w);
+      step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, sh, w);
       t[j] = xb;
       if (spec) {
         const float xoj = xo[j];
@@ -362,14 +365,15 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
       }
     }
   }
-  // slot 5: GPBB ||x - P(x - theta g)||^2, or UPN ||x+ - x||^2
-  FF acc[8] = {a0, a1, s0, s1, s2, s3, au, sb};
-  double tot[8];
-  if (grid_reduce<8>(acc, slot, tot) && threadIdx.x == 0) {
+  // slot 5: GPBB ||x - P(x - theta g)||^2, or UPN ||x+ - x||^2; slot 8: TV_tau(xbar)
+  FF acc[9] = {a0, a1, s0, s1, s2, s3, au, sb, sh};
+  double tot[9];
+  if (grid_reduce<9>(acc, slot, tot) && threadIdx.x == 0) {
     st->r_fwd[0] = tot[0];
     st->r_fwd[1] = tot[1];
 #pragma unroll
     for (int k = 0; k < 4; ++k) st->r_step[k] = tot[2 + k];
+    st->r_step[4] = tot[8];
     if (SPEC) {
       st->r_spec[0] = tot[5];
       st->r_spec[1] = tot[6];

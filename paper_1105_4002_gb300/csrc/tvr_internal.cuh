@@ -8,7 +8,7 @@
 #include "tvr.h"
 
 #define TVR_BLOCK 256          // threads per block of every streaming kernel
-#define TVR_RMAX 8             // reductions carried by one kernel
+#define TVR_RMAX 16            // reductions carried by one kernel
 #define TVR_MAX_GRID 4096      // upper bound on blocks of a reducing kernel
 #define TVR_PROF_PAIRS 4096    // timed launches held per kernel kind between harvests
 #define TVR_PROF_KINDS 4       // forward, back projection, step, UPN extrapolation
@@ -84,7 +84,7 @@ __device__ __forceinline__ FF ff_shfl_xor(FF a, int mask) {
   return b;
 }
 
-// Warp-wide reduce-scatter of R <= 8 pairs (padded to P, a power of two):
+// Warp-wide reduce-scatter of R <= 16 pairs (padded to P, a power of two):
 // each exchange step at lane distance 16, 8, ... keeps one half of the values
 // a lane carries and merges the partner's copy of that half, so that after
 // log2 P steps lane l carries value k = l / (32 / P) alone; the remaining
@@ -93,8 +93,8 @@ __device__ __forceinline__ FF ff_shfl_xor(FF a, int mask) {
 // both partners of an exchange hold the same result.
 template <int R>
 struct RedShape {
-  static_assert(R >= 1 && R <= 8, "R");
-  static constexpr int P = R == 1 ? 1 : (R == 2 ? 2 : (R <= 4 ? 4 : 8));
+  static_assert(R >= 1 && R <= 16, "R");
+  static constexpr int P = R == 1 ? 1 : (R == 2 ? 2 : (R <= 4 ? 4 : (R <= 8 ? 8 : 16)));
 };
 
 template <int R>

@@ -105,6 +105,29 @@ def parallel_geometry(n: int, directions: np.ndarray, det: int, pitch: float = 1
                     kind=KIND_PARALLEL)
 
 
+def sphere_directions(count: int) -> np.ndarray:
+    """``count`` unit vectors spread evenly over the unit sphere: the
+    golden-angle spiral (heights uniform in (-1, 1) at the midpoints of
+    ``count`` equal bands, azimuth advancing by pi (3 - sqrt 5) per point)."""
+    k = np.arange(count, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / count
+    phi = k * math.pi * (3.0 - math.sqrt(5.0))
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def sphere_parallel_geometry(n: int, views: int, det: int) -> Geometry:
+    """Parallel-beam scan with view directions spread evenly over the unit
+    sphere, det^2 pixels of unit pitch (det = 91 covers the diagonal of a 64^3
+    volume)."""
+    return parallel_geometry(n, sphere_directions(views), det)
+
+
+def noise_exact(ax: np.ndarray, z: np.ndarray, level: float) -> np.ndarray:
+    """Noise e = level * ||ax|| * z / ||z||, so that ||e|| / ||ax|| = level exactly."""
+    return level * float(np.linalg.norm(ax)) * z / float(np.linalg.norm(z))
+
+
 def ellipsoid_phantom(n: int, count: int, semi_axes: tuple[float, float],
                       values: tuple[float, float], seed: int) -> np.ndarray:
     """Piecewise-constant phantom of ``count`` axis-aligned ellipsoids.

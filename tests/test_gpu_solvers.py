@@ -54,6 +54,7 @@ def test_first_iterations_follow_the_oracle(c32, oracle_solutions, method):
         r = ref.history[i]
         assert int(h[i, 5]) == r["trials"], (i, h[i], r)
         assert abs(h[i, 1] - r["gnorm"]) <= 1e-4 * r["gnorm"], (i, h[i, 1], r["gnorm"])
+        assert abs(h[i, 6] - r["f"]) <= 1e-6 * abs(r["f"]), (i, h[i, 6], r["f"])  # phi(x^(k+1))
 
 
 @pytest.mark.parametrize("method", ["gp", "upn"])

@@ -205,3 +205,22 @@ def test_matrix_free_forward_and_adjoint_equal_the_stored_matrix():
         assert np.allclose(z, zr, rtol=1e-13, atol=1e-13 * np.abs(zr).max())
         # adjoint identity of the two on their own
         assert abs(y @ r - x @ z) <= 1e-12 * abs(y @ r)
+
+
+def test_sphere_directions_are_spread_evenly():
+    """Unit vectors; equal-area bands in height; no two directions closer than
+    a fraction of the spacing of an even covering (4 pi / count per point)."""
+    import synth
+    for count in (19, 55):
+        d = synth.sphere_directions(count)
+        assert d.shape == (count, 3)
+        assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-14)
+        assert np.allclose(np.sort(d[:, 2]), np.sort(1 - 2 * (np.arange(count) + 0.5) / count))
+        cosang = np.clip(d @ d.T - 2 * np.eye(count), -1, 1)
+        min_angle = np.arccos(cosang.max())
+        assert min_angle > 0.5 * np.sqrt(4 * np.pi / count)
+    g = synth.sphere_parallel_geometry(8, 19, 13)
+    assert g.n_views == 19 and g.m == 19 * 13 * 13
+    ax = np.random.default_rng(0).uniform(size=50)
+    e = synth.noise_exact(ax, np.random.default_rng(1).normal(size=50), 0.01)
+    assert abs(np.linalg.norm(e) / np.linalg.norm(ax) - 0.01) < 1e-15
