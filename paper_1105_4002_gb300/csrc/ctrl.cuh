@@ -2,6 +2,10 @@
 //
 // Runs in one thread (thread 0 of the block that finishes a reducing kernel),
 // in FP64, on the device-resident DevState.  No thread ever waits here.
+// A solver pass is two kernels: the back projection (gradient at the newly
+// accepted point, then ctrl_after_grad) and the trial kernel (projected step,
+// forward projection, in UPN the extrapolation for the case of acceptance,
+// then ctrl_trial).
 //
 // The acceptance tests are evaluated in Bregman form.  For f = phi and a step
 // d = xbar - p from a base point p with gradient g = grad f(p),
@@ -106,7 +110,7 @@ __device__ __forceinline__ void ctrl_init(DevState *st, const double *tot) {
 
 // After a gradient evaluation at the newly accepted point.
 // GPBB: tot[1] = <s, g_new - g_old>, tot[2] = ||s||^2, s = x^(k) - x^(k-1).
-// UPN:  tot[1] = sum_j B_h(D_j x^(k); D_j y^(k)) (from the extrapolation kernel).
+// UPN:  tot[1] = sum_j B_h(D_j x^(k); D_j y^(k)) (formed by the accepted trial).
 __device__ __forceinline__ void ctrl_after_grad(DevState *st, const double *tot) {
   st->g_evals++;
   st->need_grad = 0;

@@ -1,16 +1,20 @@
 // Hot-path kernels of the TV-CT gradient methods (sm_103a).
 //
-//   k_forward   r = A x - b (CSR, row-parallel), 1/2||r||^2; trial mode gathers (p, g),
-//               forms xbar = P_Q(p - s g) per entry for A xbar and A(xbar - p), and
-//               fuses the projected step over the voxels (g^T d, ||d||^2, sum_j B_h,
-//               the Huber weights at xbar) with the acceptance test
-//   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free) fused with
-//               the TV_tau stencil and its value; solver modes add the BB dots
-//               (GPBB) or the TV Bregman sum of the mu-estimate (UPN)
-//               (and, in UPN, the extrapolation y = x+ + beta (x+ - x) with its
-//               residual A y - b for the case of acceptance)
+//   k_forward   r = A x - b (CSR, row-parallel), 1/2||r||^2.  Trial modes (the
+//               second kernel of a solver pass) gather (p, g) pairs, form
+//               xbar = P_Q(p - s g) per entry for A xbar and A(xbar - p), fuse
+//               the projected step over the voxels (g^T d, ||d||^2, sum_j B_h,
+//               TV_tau(xbar), the Huber weights of the next gradient point) and,
+//               in UPN, the extrapolation y = x+ + beta (x+ - x) with its residual
+//               A y - b for the case of acceptance; the last block runs the test
+//   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free); plain
+//               modes fuse the TV_tau stencil and its value, the solver mode
+//               reads the TV gradient from the Huber weight planes and adds the
+//               BB dots (GPBB); it also writes the (p, g) pairs of the next trial
 //   k_tv_value  TV_tau(x) alone (phi without a gradient)
 //   k_project   P_Q in place; k_gmap gradient-map norm
+// Matrix-free storage (template flag MF) replaces the CSR / CSC loops by the
+// on-the-fly entries of mf.cuh.
 //
 // All reductions: double-single per thread / warp / block, deterministic
 // block-ordered finish in the last block (tvr_internal.cuh).

@@ -304,7 +304,7 @@ struct DevState {
   // control scalars
   double L, Lt, theta, beta, beta_prev, mu, M;
   int M_valid;
-  double step, step2;           // step size of the step kernel; GPBB: theta for G
+  double step, step2;           // step size of the trial's projected step; GPBB: theta for G
   double f_cur, fhist[TVR_FHIST];
   int nhist;
   double gnorm, gnorm0, stopval, gnorm_trial;
@@ -326,10 +326,10 @@ struct DevState {
                // written by the back projection (solver and init modes)
   // Huber weights w_e(D_j v) of the point v where the next gradient is taken,
   // as 4 planes of N floats: w_0, w_1, w_2 and (w_0 + w_1) + w_2.  `w` holds
-  // them for the gradient point (written by the extrapolation kernel in UPN),
-  // `wt` for the trial point of GP / GPBB (written by the step kernel; the
-  // two swap on acceptance).  The back projection then reads the TV gradient
-  // instead of re-evaluating the stencil.
+  // them for the current gradient point; each trial writes `wt` for the point
+  // its acceptance would make the next gradient point (xbar for GP / GPBB, y
+  // for UPN), and the two swap on acceptance.  The back projection then reads
+  // the TV gradient instead of re-evaluating the stencil.
   float *w, *wt;
   // history (device buffer of hist_cap records)
   double *hist;
