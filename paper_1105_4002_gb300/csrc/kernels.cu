@@ -57,17 +57,42 @@ __device__ __forceinline__ float group_sum(float v) {
 
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
+// Loads of the streamed matrix arrays (indices, values): read once per
+// projection, so they bypass L1 allocation and leave L1 to the gathered
+// vector, which neighbouring rows and columns reuse.
+__device__ __forceinline__ int4 ld_stream(const int32_t *p) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float *p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream2(const void *p) {
+  uint2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p));
+  return v;
+}
+
 // Four stored values at a 4-aligned position: float32, or bfloat16 codes
 // widened to float32 (a bfloat16 is the upper half of a float32's bits).
 template <bool BF>
 __device__ __forceinline__ float4 load4(const float *__restrict__ v32,
                                         const __nv_bfloat16 *__restrict__ v16, int64_t e) {
   if (BF) {
-    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(v16 + e));
+    const uint2 raw = ld_stream2(v16 + e);
     return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
                        __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
   }
-  return __ldg(reinterpret_cast<const float4 *>(v32 + e));
+  return ld_stream(v32 + e);
 }
 
 __device__ __forceinline__ float xbar_of(float p, float g, float s) {
@@ -234,7 +259,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
     int4 cn = make_int4(0, 0, 0, 0);
     float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e0 < end) {
-      cn = __ldg(reinterpret_cast<const int4 *>(A.col + e0));
+      cn = ld_stream(A.col + e0);
       vn = load4<BF>(A.val, A.qval, e0);
     }
     for (; e0 < end; e0 += 4 * G) {
@@ -246,7 +271,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         const float2 q0 = __ldg(pg + c4.x), q1 = __ldg(pg + c4.y);
         const float2 q2 = __ldg(pg + c4.z), q3 = __ldg(pg + c4.w);
         if (e1 < end) {
-          cn = __ldg(reinterpret_cast<const int4 *>(A.col + e1));
+          cn = ld_stream(A.col + e1);
           vn = load4<BF>(A.val, A.qval, e1);
         }
         const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
@@ -263,7 +288,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         const float x0 = __ldg(x + c4.x), x1 = __ldg(x + c4.y);
         const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
         if (e1 < end) {
-          cn = __ldg(reinterpret_cast<const int4 *>(A.col + e1));
+          cn = ld_stream(A.col + e1);
           vn = load4<BF>(A.val, A.qval, e1);
         }
         sx = __fmaf_rn(v4.x, x0, sx);
@@ -473,7 +498,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
     int4 in4 = make_int4(0, 0, 0, 0);
     float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e0 < end) {
-      in4 = __ldg(reinterpret_cast<const int4 *>(A.row + e0));
+      in4 = ld_stream(A.row + e0);
       vn = load4<BF>(A.cval, A.qcval, e0);
     }
     for (; e0 < end; e0 += 4 * G) {
@@ -483,7 +508,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
       float r2 = __ldg(r + i4.z), r3 = __ldg(r + i4.w);
       const int64_t e1 = e0 + 4 * G;
       if (e1 < end) {
-        in4 = __ldg(reinterpret_cast<const int4 *>(A.row + e1));
+        in4 = ld_stream(A.row + e1);
         vn = load4<BF>(A.cval, A.qcval, e1);
       }
       if (BF && (MODE == BWD_ADJ || MODE == BWD_VJP)) {  // caller's r: apply the row scales
