@@ -57,31 +57,6 @@ __device__ __forceinline__ float group_sum(float v) {
 
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
-// Loads of the streamed matrix arrays (indices, values): read once per
-// projection, so they bypass L1 allocation and leave L1 to the gathered
-// vector, which neighbouring rows and columns reuse.
-__device__ __forceinline__ int4 ld_stream(const int32_t *p) {
-  int4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
-}
-__device__ __forceinline__ float4 ld_stream(const float *p) {
-  float4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
-}
-__device__ __forceinline__ uint2 ld_stream2(const void *p) {
-  uint2 v;
-  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
-               : "=r"(v.x), "=r"(v.y)
-               : "l"(p));
-  return v;
-}
-
 // Four stored values at a 4-aligned position: float32, or bfloat16 codes
 // widened to float32 (a bfloat16 is the upper half of a float32's bits).
 template <bool BF>
@@ -651,14 +626,29 @@ int occupancy_grid(const void *kernel, int block, int device) {
   return g < TVR_MAX_GRID ? g : TVR_MAX_GRID;
 }
 
-void kernel_grids(Workspace &ws, int device) {
-  ws.grid_fwd =
-      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device);
-  ws.grid_trial_x =
-      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_X, false>, TVR_BLOCK, device);
-  ws.grid_bwd =
-      occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device);
-  ws.grid_elem = occupancy_grid((const void *)k_tv_value, TVR_BLOCK, device);
+void kernel_grids(Workspace &ws, int device, int64_t m, int64_t N) {
+  // at most one wave of resident blocks, and no more blocks than the work
+  // needs (rows or columns in groups of TVR_BLOCK / lanes, voxels in groups of
+  // TVR_BLOCK), so that the kernels of small systems leave room for others
+  // running concurrently on other streams
+  auto cap = [](int grid, int64_t need) {
+    need = need < 1 ? 1 : need;
+    return (int)(need < grid ? need : grid);
+  };
+  const int64_t rows = (m + TVR_BLOCK / kRowLanes - 1) / (TVR_BLOCK / kRowLanes);
+  const int64_t cols = (N + TVR_BLOCK / kColLanes - 1) / (TVR_BLOCK / kColLanes);
+  const int64_t vox = (N + TVR_BLOCK - 1) / TVR_BLOCK;
+  const int64_t fwd_need = rows > vox ? rows : vox;
+  ws.grid_fwd = cap(
+      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device),
+      fwd_need);
+  ws.grid_trial_x = cap(
+      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_X, false>, TVR_BLOCK, device),
+      fwd_need);
+  ws.grid_bwd = cap(
+      occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device),
+      cols);
+  ws.grid_elem = cap(occupancy_grid((const void *)k_tv_value, TVR_BLOCK, device), vox);
 }
 
 // Launch with programmatic stream serialization (the kernel calls pdl_enter

@@ -146,14 +146,14 @@ __global__ void __launch_bounds__(TVR_BLOCK)
 #pragma unroll
     for (int c = 0; c < KS; ++c) s0[c] = s1[c] = 0.f;
     for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4 *>(A.col + e0));
+      const int4 c4 = ld_stream(A.col + e0);
       float4 v4;
       if (BF) {
-        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(A.qval + e0));
+        const uint2 raw = ld_stream2(A.qval + e0);
         v4 = make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
                          __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
       } else {
-        v4 = __ldg(reinterpret_cast<const float4 *>(A.val + e0));
+        v4 = ld_stream(A.val + e0);
       }
       const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
       const float vs[4] = {v4.x, v4.y, v4.z, v4.w};
@@ -218,14 +218,14 @@ __global__ void __launch_bounds__(TVR_BLOCK)
 #pragma unroll
     for (int c = 0; c < KS; ++c) s[c] = 0.f;
     for (int64_t e0 = beg + 4 * lane; e0 < end; e0 += 4 * G) {
-      const int4 i4 = __ldg(reinterpret_cast<const int4 *>(A.row + e0));
+      const int4 i4 = ld_stream(A.row + e0);
       float4 v4;
       if (BF) {
-        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(A.qcval + e0));
+        const uint2 raw = ld_stream2(A.qcval + e0);
         v4 = make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
                          __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
       } else {
-        v4 = __ldg(reinterpret_cast<const float4 *>(A.cval + e0));
+        v4 = ld_stream(A.cval + e0);
       }
       const int is[4] = {i4.x, i4.y, i4.z, i4.w};
       const float vs[4] = {v4.x, v4.y, v4.z, v4.w};

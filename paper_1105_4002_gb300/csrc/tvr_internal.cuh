@@ -386,6 +386,31 @@ struct MatDev {
   int V, Pu, Pv, kind;
 };
 
+// Loads of the streamed matrix arrays (indices, values): read once per
+// projection, so they bypass L1 allocation and leave L1 to the gathered
+// vector, which neighbouring rows and columns reuse.
+__device__ __forceinline__ int4 ld_stream(const int32_t *p) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float *p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream2(const void *p) {
+  uint2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p));
+  return v;
+}
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialization may be scheduled while its predecessor on the stream is still
 // running.  It lets its own successor do the same, then waits until the
@@ -505,4 +530,4 @@ cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream
 void free_matrix(MatStore &A);
 
 int occupancy_grid(const void *kernel, int block, int device);
-void kernel_grids(Workspace &ws, int device);
+void kernel_grids(Workspace &ws, int device, int64_t m, int64_t N);
