@@ -522,7 +522,8 @@ namespace {
 // One thread per view: the FP64 record rounded to float32, the detector
 // normal (oriented away from the source) and the dual basis of (u, w) in the
 // detector plane, all formed in FP64 with explicit rounding.
-__global__ void k_mf_views(const ViewRec *__restrict__ views, int V, MfView *__restrict__ out) {
+__global__ void k_mf_views(const ViewRec *__restrict__ views, int V, int kind,
+                           MfView *__restrict__ out) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const double *r = views[v].v;
@@ -554,7 +555,43 @@ __global__ void k_mf_views(const ViewRec *__restrict__ views, int V, MfView *__r
     o.ww[k] = g > 0.0 ? (float)ddiv(dsub(dmul(guu, w[k]), dmul(guw, u[k])), g) : 0.f;
   }
   o.dn = (float)dn;
-  o.pad[0] = o.pad[1] = 0.f;
+  // projection constants (see MfView): cone a0 = (src - det) . uu; parallel
+  // ga = uu - nrm (dir . uu) / (dir . nrm) with dir = det - src, a0 = -det . ga
+  double uu[3], ww[3], dir[3];
+  for (int k = 0; k < 3; ++k) {
+    uu[k] = g > 0.0 ? ddiv(dsub(dmul(gww, u[k]), dmul(guw, w[k])), g) : 0.0;
+    ww[k] = g > 0.0 ? ddiv(dsub(dmul(guu, w[k]), dmul(guw, u[k])), g) : 0.0;
+    dir[k] = dsub(det[k], src[k]);
+  }
+  double du = 0.0, dw = 0.0, dd = 0.0, a0 = 0.0, b0 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    du = dadd(du, dmul(dir[k], uu[k]));
+    dw = dadd(dw, dmul(dir[k], ww[k]));
+    dd = dadd(dd, dmul(dir[k], nr[k]));
+  }
+  double ga[3], gb[3];
+  for (int k = 0; k < 3; ++k) {
+    ga[k] = dd != 0.0 ? dsub(uu[k], ddiv(dmul(nr[k], du), dd)) : 0.0;
+    gb[k] = dd != 0.0 ? dsub(ww[k], ddiv(dmul(nr[k], dw), dd)) : 0.0;
+  }
+  if (kind == TVR_PARALLEL) {
+    for (int k = 0; k < 3; ++k) {
+      a0 = dsub(a0, dmul(det[k], ga[k]));
+      b0 = dsub(b0, dmul(det[k], gb[k]));
+    }
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      a0 = dadd(a0, dmul(dsub(src[k], det[k]), uu[k]));
+      b0 = dadd(b0, dmul(dsub(src[k], det[k]), ww[k]));
+    }
+  }
+  o.a0 = (float)a0;
+  o.b0 = (float)b0;
+  for (int k = 0; k < 3; ++k) {
+    o.ga[k] = (float)ga[k];
+    o.gb[k] = (float)gb[k];
+  }
+  for (int k = 0; k < 7; ++k) o.pad[k] = 0.f;
   out[v] = o;
 }
 
@@ -574,7 +611,7 @@ cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int
   (void)n;
   BM_TRY(owned(&A.mfv, V));
   k_mf_views<<<(V + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), V,
-                                              A.mfv);
+                                              kind, A.mfv);
   BM_TRY(cudaGetLastError());
   return cudaStreamSynchronize(s);
 }

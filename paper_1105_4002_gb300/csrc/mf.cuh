@@ -29,9 +29,14 @@
 struct MfView {
   float src[3], det[3], u[3], w[3];
   float nrm[3];       // unit normal of the detector plane
-  float uu[3], ww[3]; // u / |u|^2 and w / |w|^2: pixel coordinates of a detector-plane offset
+  float uu[3], ww[3]; // dual basis of (u, w): pixel coordinates of a detector-plane offset
   float dn;           // (det - src) . nrm
-  float pad[2];
+  // pixel coordinates a, b of the projection of a point X:
+  //   cone:     a = a0 + dn ((X - src) . uu) / ((X - src) . nrm), b likewise with ww
+  //   parallel: a = ga . X + a0, b = gb . X + b0 (linear)
+  float a0, b0;
+  float ga[3], gb[3];
+  float pad[7];
 };
 
 struct MfRay {
@@ -160,51 +165,55 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int 
   const float ca = 0.5f * (float)(Pu - 1), cb = 0.5f * (float)(Pv - 1);
   for (int vi = lane; vi < V; vi += G) {
     const MfView &v = views[vi];
-    // pixel-coordinate box of the projected corners
+    // pixel-coordinate box of the voxel's projection: the extremes of a
+    // projective (cone) or linear (parallel) map over a box lie at corners
     float amin = 3.4e38f, amax = -3.4e38f, bmin = 3.4e38f, bmax = -3.4e38f;
     bool ok = true;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float X[3] = {__fsub_rn((float)(ix + (c & 1)), half),
-                          __fsub_rn((float)(iy + ((c >> 1) & 1)), half),
-                          __fsub_rn((float)(iz + ((c >> 2) & 1)), half)};
-      float P[3];
-      if (kind == TVR_PARALLEL) {
-        // along the common direction det - src onto the detector plane
-        float dir[3], num = 0.f, den = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          dir[k] = __fsub_rn(v.det[k], v.src[k]);
-          num = __fadd_rn(num, __fmul_rn(__fsub_rn(v.det[k], X[k]), v.nrm[k]));
-          den = __fadd_rn(den, __fmul_rn(dir[k], v.nrm[k]));
-        }
-        const float t = __fdiv_rn(num, den);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) P[k] = __fadd_rn(X[k], __fmul_rn(t, dir[k]));
-      } else {
-        // central projection from the source onto the detector plane
-        float e[3], den = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          e[k] = __fsub_rn(X[k], v.src[k]);
-          den = __fadd_rn(den, __fmul_rn(e[k], v.nrm[k]));
-        }
-        ok = ok && den > 0.f;  // a corner at or behind the source plane: use the whole detector
-        const float t = __fdiv_rn(v.dn, den);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) P[k] = __fadd_rn(v.src[k], __fmul_rn(t, e[k]));
-      }
-      float a = 0.f, b = 0.f;
+    const float X0[3] = {__fsub_rn((float)ix, half), __fsub_rn((float)iy, half),
+                         __fsub_rn((float)iz, half)};
+    if (kind == TVR_PARALLEL) {
+      float ac = v.a0, bc = v.b0, ra = 0.f, rb = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float o = __fsub_rn(P[k], v.det[k]);
-        a = __fadd_rn(a, __fmul_rn(o, v.uu[k]));
-        b = __fadd_rn(b, __fmul_rn(o, v.ww[k]));
+        const float xc = __fadd_rn(X0[k], 0.5f);
+        ac = __fmaf_rn(v.ga[k], xc, ac);
+        bc = __fmaf_rn(v.gb[k], xc, bc);
+        ra = __fmaf_rn(0.5f, fabsf(v.ga[k]), ra);
+        rb = __fmaf_rn(0.5f, fabsf(v.gb[k]), rb);
       }
-      amin = fminf(amin, a);
-      amax = fmaxf(amax, a);
-      bmin = fminf(bmin, b);
-      bmax = fmaxf(bmax, b);
+      amin = ac - ra;
+      amax = ac + ra;
+      bmin = bc - rb;
+      bmax = bc + rb;
+    } else {
+      // numerators and denominator at the lower corner, then per corner the
+      // sums of the components its offset adds
+      float na = 0.f, nb = 0.f, nd = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float e = __fsub_rn(X0[k], v.src[k]);
+        na = __fmaf_rn(e, v.uu[k], na);
+        nb = __fmaf_rn(e, v.ww[k], nb);
+        nd = __fmaf_rn(e, v.nrm[k], nd);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float ca_ = na, cb_ = nb, cd = nd;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if ((c >> k) & 1) {
+            ca_ = __fadd_rn(ca_, v.uu[k]);
+            cb_ = __fadd_rn(cb_, v.ww[k]);
+            cd = __fadd_rn(cd, v.nrm[k]);
+          }
+        ok = ok && cd > 0.f;  // a corner at or behind the source plane: use the whole detector
+        const float s = __fmul_rn(v.dn, __frcp_rn(cd));
+        const float a = __fmaf_rn(s, ca_, v.a0), b = __fmaf_rn(s, cb_, v.b0);
+        amin = fminf(amin, a);
+        amax = fmaxf(amax, a);
+        bmin = fminf(bmin, b);
+        bmax = fmaxf(bmax, b);
+      }
     }
     int p0 = 0, p1 = Pu - 1, q0 = 0, q1 = Pv - 1;  // whole detector unless the box is sound
     const float lim = 1e7f;
@@ -218,12 +227,24 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int 
       p1 = p1 > Pu - 1 ? Pu - 1 : p1;
       q1 = q1 > Pv - 1 ? Pv - 1 : q1;
     }
+    // pixels in groups of 4 along a detector row: the entries first, then
+    // the gathers of the group together
     for (int q = q0; q <= q1; ++q)
-      for (int p = p0; p <= p1; ++p) {
-        MfRay r;
-        mf_pixel_ray(v, kind, Pu, Pv, p, q, r);
-        const float len = mf_len(r, ix, iy, iz, half);
-        if (len > 0.f) use(((int64_t)vi * Pv + q) * Pu + p, len);
+      for (int p = p0; p <= p1; p += 4) {
+        float lv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          lv[t] = 0.f;
+          if (p + t <= p1) {
+            MfRay r;
+            mf_pixel_ray(v, kind, Pu, Pv, p + t, q, r);
+            lv[t] = mf_len(r, ix, iy, iz, half);
+          }
+        }
+        const int64_t i0 = ((int64_t)vi * Pv + q) * Pu + p;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (lv[t] > 0.f) use(i0 + t, lv[t]);
       }
   }
 }
