@@ -578,9 +578,9 @@ def main():
     # ---- timed region ----
     sampler = ClockSampler(gpu_id_for(torch, dev))
     # the timed region times only the dominant kernel (the trial forward
-    # projection), on every 8th pass: event nodes around every kernel would
+    # projection), on every 32nd pass: event nodes around every kernel would
     # slow the graphs
-    sysm.profile(True, kinds=("forward",), sample_stride=8)
+    sysm.profile(True, kinds=("forward",), sample_stride=32)
     sysm.profile_read()
     if dist:
         dist.barrier()
@@ -703,7 +703,7 @@ def main():
                 "traffic": trial_traffic, "kernel": "fwd_csr_trial",
                 "launches": nf, "avg_us": 1e6 * avg_s, "algorithmic_bytes_per_launch": bytes_fwd,
                 "peak_source": peak_kind,
-                "timing": "CUDA event nodes around the kernel in every 8th pass of the timed "
+                "timing": "CUDA event nodes around the kernel in every 32nd pass of the timed "
                           "region (launches that did work only)",
                 "breakdown_us": bk,
                 "breakdown_frac": {"forward": bytes_fwd / (bk["forward"] / 1e6) / 1e9 / peak,
