@@ -592,7 +592,7 @@ def main():
     evals = 0
     passes = 0
     launches = 0
-    trials_gpbb = trials_upn = 0
+    passes_gpbb = passes_upn = 0
     t_gpbb, t_upn, it_gpbb, it_upn = [], [], [], []
     for _ in range(args.steps):
         s0 = time.perf_counter()
@@ -606,8 +606,8 @@ def main():
         it_upn.append(r2.iters)
         evals += r1.g_evals + r2.g_evals
         passes += r1.passes + r2.passes
-        trials_gpbb += r1.f_evals - 1
-        trials_upn += r2.f_evals - 1
+        passes_gpbb += r1.passes
+        passes_upn += r2.passes
         # init (2) + per pass (2 GPBB / 3 UPN: the step is fused into the trial forward)
         # + final phi (2)
         launches += 2 + 2 * r1.passes + 2 + 2 + 3 * r2.passes + 2
@@ -681,13 +681,14 @@ def main():
     # the four Huber weight planes, x read and g and (p, g) written
     bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
     # trial kernel: A (values + indices), row pointers, the (p, g) pairs read and
-    # xbar written, b read and r written; GP / GPBB trials write the four Huber
-    # weight planes at xbar; UPN trials read u and x and write u, A y - b, y and
+    # xbar written, b read and r written; GPBB trials (two points per pass)
+    # write the four Huber weight planes at both points and the second point's
+    # xbar and residual; UPN trials read u and x and write u, A y - b, y and
     # the planes at y (the extrapolation for the case of acceptance).  Weighted
-    # by the share of each method's trials among the timed launches.
-    w_share = trials_gpbb / max(trials_gpbb + trials_upn, 1)
+    # by the share of each method's trial launches among the timed launches.
+    w_share = passes_gpbb / max(passes_gpbb + passes_upn, 1)
     bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
-                 + w_share * 16 * N + (1 - w_share) * (12 * m + 24 * N))
+                 + w_share * (16 * N + 4 * m + 20 * N) + (1 - w_share) * (12 * m + 24 * N))
     # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
     t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage)
     t_u = captured_traffic("fwd_csr_trial_upn", args.storage)

@@ -227,7 +227,11 @@ typedef struct tvr_solve_opts {
   int32_t bt_max;           /* increases of L per BT call (default 60) */
   int32_t use_graph;        /* 1 (default): batches of passes replayed as CUDA graphs */
   int32_t batch;            /* passes launched between host checks (default 32) */
-  int32_t reserved;
+  int32_t gpbb_points;      /* GPBB trial points per forward pass: 2 (default; 0 means 2) or 1.
+                               With 2, each pass also forms the trial the line search takes
+                               after a rejection (step beta^2 theta) and uses it when the first
+                               is rejected: the same decisions and iterates as one point per
+                               pass, in fewer passes over A */
   double gpbb_sigma;        /* default 0.1 (Sec. III-A) */
   double gpbb_beta0;        /* default 0.95 (Alg. 1) */
   double rho_L;             /* BT factor (Alg. 2), default 2 */

@@ -70,6 +70,7 @@ class SolveOptions:
     bt_max: int = 60
     use_graph: bool = True
     batch: int = 32
+    gpbb_points: int = 2  # GPBB trial points per forward pass (1 or 2; same iterates)
     gpbb_sigma: float = 0.1
     gpbb_beta0: float = 0.95
     rho_L: float = 2.0
@@ -213,7 +214,7 @@ class System:
         co = _capi.SolveOpts()
         lib().tvr_solve_opts_default(ctypes.byref(co))
         for f in ("k_max", "stop_mode", "gpbb_K", "gpbb_max_trials", "bt_max", "batch",
-                  "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
+                  "gpbb_points", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
             setattr(co, f, getattr(o, f))
         co.use_graph = 1 if o.use_graph else 0
         hist = None
@@ -258,7 +259,7 @@ class System:
         co = _capi.SolveOpts()
         lib().tvr_solve_opts_default(ctypes.byref(co))
         for f in ("k_max", "stop_mode", "gpbb_K", "gpbb_max_trials", "bt_max", "batch",
-                  "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
+                  "gpbb_points", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
             setattr(co, f, getattr(o, f))
         co.use_graph = 1 if o.use_graph else 0
         return co

@@ -36,7 +36,8 @@ class Geometry(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("stop_mode", ctypes.c_int32), ("gpbb_K", ctypes.c_int32),
                 ("gpbb_max_trials", ctypes.c_int32), ("bt_max", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("gpbb_points", ctypes.c_int32),
                 ("gpbb_sigma", ctypes.c_double), ("gpbb_beta0", ctypes.c_double),
                 ("rho_L", ctypes.c_double), ("L_bar", ctypes.c_double), ("mu_bar", ctypes.c_double),
                 ("history", ctypes.c_void_p), ("history_len", ctypes.c_int64)]

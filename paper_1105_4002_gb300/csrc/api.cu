@@ -96,7 +96,7 @@ int tvr_system_free(tvr_system *sys) {
   if (sys->stage_sweepX) cudaFree(sys->stage_sweepX);
   void *ptrs[] = {sys->ws_mem, sys->stage_xN, sys->stage_gN, sys->stage_bM, sys->stage_rM,
                   sys->phi_ws, sys->st, sys->hist_dev, sys->prof_flags_dev, sys->pg,
-                  sys->wplanes[0], sys->wplanes[1]};
+                  sys->wplanes[0], sys->wplanes[1], sys->wplanes[2]};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (float *p : sys->vN)
@@ -423,6 +423,7 @@ void tvr_solve_opts_default(tvr_solve_opts *o) {
   o->bt_max = 60;
   o->use_graph = 1;
   o->batch = 32;
+  o->gpbb_points = 2;
   o->gpbb_sigma = 0.1;
   o->gpbb_beta0 = 0.95;
   o->rho_L = 2.0;

@@ -257,3 +257,27 @@ __device__ __forceinline__ void ctrl_trial(DevState *st, const double *fwd) {
   st_hist(st, st->k - 1, st->gnorm, st->L, st->solver == SOLVER_UPN ? st->mu : 0.0,
           st->solver == SOLVER_UPN ? st->beta : 0.0, tr, st->f_cur, st->stopval);
 }
+
+// GPBB with two trial points per pass: fwd = {||A xbar - b||^2, ||A d||^2} of
+// the first point (its step sums in r_step); the second point, at the step
+// beta^2 theta that a rejection of the first leads to, has its sums in
+// r_fwd2 / r_step2 and its vectors in the roles T2, RT2, RTS2, wt2.  The
+// first is tested as usual; if it is rejected (and the trial cap not hit),
+// the roles of the second point move into place and it is tested as the next
+// trial, so the decisions and iterates are those of one point per pass.
+__device__ __forceinline__ void ctrl_trial2(DevState *st, const double *fwd) {
+  const int k0 = st->k;
+  ctrl_trial(st, fwd);
+  if (st->done || st->k != k0) return;  // accepted, or stopped
+  st_swap(st->vN[RN_T], st->vN[RN_T2]);
+  st_swap(st->vM[RM_RT], st->vM[RM_RT2]);
+  st_swap(st->vM[RM_RTS], st->vM[RM_RTS2]);
+  st_swap(st->wt, st->wt2);
+  st->r_fwd[0] = st->r_fwd2[0];
+  st->r_fwd[1] = st->r_fwd2[1];
+  st->r_step[0] = st->r_step2[0];
+  st->r_step[1] = st->r_step2[1];
+  st->r_step[2] = st->r_step2[2];
+  st->r_step[4] = st->r_step2[3];
+  ctrl_trial(st, st->r_fwd2);
+}

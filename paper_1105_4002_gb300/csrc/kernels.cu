@@ -136,9 +136,11 @@ __device__ __forceinline__ void yform_voxel(float xn, float yj, const float xk[3
 }
 
 // FWD_TRIAL_X: the UPN trial, which also forms the extrapolation for the
-// case of acceptance (a separate instance, so that the GP / GPBB trial keeps
-// its register budget).
-enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3, FWD_TRIAL_X = 4 };
+// case of acceptance; FWD_TRIAL_2: the GPBB trial with two points (steps
+// beta theta and beta^2 theta).  Separate instances, so that the GP / GPBB
+// single-point trial keeps its register budget.
+enum FwdMode { FWD_RESID = 0, FWD_Y = 1, FWD_INIT = 2, FWD_TRIAL = 3, FWD_TRIAL_X = 4,
+               FWD_TRIAL_2 = 5 };
 enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP = 4 };
 
 // ---------------------------------------------------------------------------
@@ -146,17 +148,21 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool BF, bool MF = false>
-__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR_TRIAL_MIN_BLOCKS
-                                                                            : TVR_FWD_MIN_BLOCKS))
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
+                                            : (MODE == FWD_TRIAL_X || MODE == FWD_TRIAL_2
+                                                   ? TVR_TRIAL_MIN_BLOCKS
+                                                   : TVR_FWD_MIN_BLOCKS))
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
               float *__restrict__ rout, RedSlot slot, DevState *st, int prof_slot = -1,
               float *__restrict__ rsout = nullptr) {
-  constexpr bool TRIAL = MODE == FWD_TRIAL || MODE == FWD_TRIAL_X;
+  constexpr bool TRIAL = MODE == FWD_TRIAL || MODE == FWD_TRIAL_X || MODE == FWD_TRIAL_2;
   constexpr bool SPEC = MODE == FWD_TRIAL_X;
+  constexpr bool TWO = MODE == FWD_TRIAL_2;
   pdl_enter();
   const float *x = xin;
   const float2 *pg = nullptr;  // trial mode: (p_j, g_j) per voxel
   float s = 0.f;               // trial mode: step size
+  float sq = 0.f;              // two-point trial: step of the second point
   float *r = rout;
   float *rs = rsout;           // BF16 storage: r times the row scale
   // UPN: the extrapolation for the case of acceptance (see DevState::spec_upn)
@@ -177,6 +183,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
     s = (float)st->step;
     r = st->vM[RM_RT];
     rs = st->vM[RM_RTS];
+    if (TWO) sq = (float)((st->beta * st->beta) * st->theta);  // the step after a rejection
     if (SPEC) {
       __shared__ float sh_bnew;
       u_old = st->vM[RM_U];
@@ -198,6 +205,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
   const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
   const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
   FF a0 = ff_zero(), a1 = ff_zero(), au = ff_zero();
+  FF c0 = ff_zero(), c1 = ff_zero();  // two-point trial: the second point's residual sums
   for (int64_t base = warp * RPW; base < A.m; base += nwarp * RPW) {
     const int64_t row = base + sub;
     const bool valid = row < A.m;
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
       beg = __ldg(A.row_ptr + row);
       end = __ldg(A.row_ptr + row + 1);
     }
-    float sx = 0.f, sd = 0.f;
+    float sx = 0.f, sd = 0.f, sx2 = 0.f, sd2 = 0.f;
     if (MF && valid) {
       // matrix-free: the entries of the row from the ray geometry (mf.cuh)
       const int64_t per = (int64_t)A.Pu * A.Pv;
@@ -221,6 +229,11 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
           const float bc = xbar_of(qc.x, qc.y, s);
           sx = __fmaf_rn(v, bc, sx);
           sd = __fmaf_rn(v, __fsub_rn(bc, qc.x), sd);
+          if (TWO) {
+            const float bc2 = xbar_of(qc.x, qc.y, sq);
+            sx2 = __fmaf_rn(v, bc2, sx2);
+            sd2 = __fmaf_rn(v, __fsub_rn(bc2, qc.x), sd2);
+          }
         } else {
           sx = __fmaf_rn(v, __ldg(x + c), sx);
         }
@@ -259,6 +272,18 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         sd = __fmaf_rn(v4.z, __fsub_rn(b2, q2.x), sd);
         sx = __fmaf_rn(v4.w, b3, sx);
         sd = __fmaf_rn(v4.w, __fsub_rn(b3, q3.x), sd);
+        if (TWO) {  // the second point, from the same gathered pairs
+          const float e0_ = xbar_of(q0.x, q0.y, sq), e1_ = xbar_of(q1.x, q1.y, sq);
+          const float e2_ = xbar_of(q2.x, q2.y, sq), e3_ = xbar_of(q3.x, q3.y, sq);
+          sx2 = __fmaf_rn(v4.x, e0_, sx2);
+          sd2 = __fmaf_rn(v4.x, __fsub_rn(e0_, q0.x), sd2);
+          sx2 = __fmaf_rn(v4.y, e1_, sx2);
+          sd2 = __fmaf_rn(v4.y, __fsub_rn(e1_, q1.x), sd2);
+          sx2 = __fmaf_rn(v4.z, e2_, sx2);
+          sd2 = __fmaf_rn(v4.z, __fsub_rn(e2_, q2.x), sd2);
+          sx2 = __fmaf_rn(v4.w, e3_, sx2);
+          sd2 = __fmaf_rn(v4.w, __fsub_rn(e3_, q3.x), sd2);
+        }
       } else {
         const float x0 = __ldg(x + c4.x), x1 = __ldg(x + c4.y);
         const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
@@ -274,12 +299,20 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
     }
     sx = group_sum<G>(sx);
     if (TRIAL) sd = group_sum<G>(sd);
+    if (TWO) {
+      sx2 = group_sum<G>(sx2);
+      sd2 = group_sum<G>(sd2);
+    }
     if (valid && lane == 0) {
       float sc = 1.f;
       if (BF) {
         sc = __ldg(A.rscale + row);
         sx = __fmul_rn(sc, sx);
         sd = __fmul_rn(sc, sd);
+        if (TWO) {
+          sx2 = __fmul_rn(sc, sx2);
+          sd2 = __fmul_rn(sc, sd2);
+        }
       }
       if (MODE == FWD_Y) {
         r[row] = sx;
@@ -290,6 +323,13 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         ff_add_prod(a0, ri, ri);
         if (TRIAL) {
           ff_add_prod(a1, sd, sd);
+          if (TWO) {
+            const float ri2 = __fsub_rn(sx2, __ldg(b + row));
+            st->vM[RM_RT2][row] = ri2;
+            if (BF) st->vM[RM_RTS2][row] = __fmul_rn(sc, ri2);
+            ff_add_prod(c0, ri2, ri2);
+            ff_add_prod(c1, sd2, sd2);
+          }
           if (SPEC) {  // UPN: u and A y - b for the case of acceptance (residual by linearity)
             const float un = __fmaf_rn(bcur, u_old[row], sd);
             u2[row] = un;
@@ -320,6 +360,8 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
   // eq. mu_k_estimate), recomputing y at the forward neighbours.
   FF s0 = ff_zero(), s1 = ff_zero(), s2 = ff_zero(), s3 = ff_zero(), sb = ff_zero();
   FF sh = ff_zero();  // TV_tau(xbar)
+  // two-point trial: the second point's g^T d, ||d||^2, sum B_h, TV_tau
+  FF d0 = ff_zero(), d1 = ff_zero(), d2 = ff_zero(), dh = ff_zero();
   {
     const bool upn = st->solver == SOLVER_UPN;
     constexpr bool spec = SPEC;
@@ -340,16 +382,31 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
       voxel_of(A, j, ix, iy, iz);
       const int64_t off[3] = {1, n, nn};
       const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
-      float pk[3], xk[3];
+      float pk[3], gk[3], xk[3];
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
         const float2 qk = in[e] ? pg[j + off[e]] : make_float2(0.f, 0.f);
         pk[e] = qk.x;
+        gk[e] = qk.y;
         xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
       }
       float w[3];
       step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, sh, w);
       t[j] = xb;
+      if (TWO) {  // the second point, as a trial at step sq would form it
+        const float xq = xbar_of(q.x, q.y, sq);
+        float xkq[3], wq[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) xkq[e] = in[e] ? xbar_of(pk[e], gk[e], sq) : 0.f;
+        FF unused = ff_zero();
+        step_voxel(q.x, q.y, xq, pk, xkq, in, sg2, false, tau, d0, d1, d2, unused, dh, wq);
+        st->vN[RN_T2][j] = xq;
+        float *__restrict__ wq_ = st->wt2;
+        wq_[j] = wq[0];
+        wq_[N + j] = wq[1];
+        wq_[2 * N + j] = wq[2];
+        wq_[3 * N + j] = __fadd_rn(__fadd_rn(wq[0], wq[1]), wq[2]);
+      }
       if (spec) {
         const float xoj = xo[j];
         const float dx = __fsub_rn(xb, xoj);
@@ -368,6 +425,25 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : (MODE == FWD_TRIAL_X ? TVR
         wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
       }
     }
+  }
+  if constexpr (TWO) {
+    // {first point: ||r||^2, ||A d||^2, g^T d, ||d||^2, sum B_h, ||x - P(x - theta g)||^2,
+    //  TV_tau; second point: ||r||^2, ||A d||^2, g^T d, ||d||^2, sum B_h, TV_tau}
+    FF acc[13] = {a0, a1, s0, s1, s2, s3, sh, c0, c1, d0, d1, d2, dh};
+    double tot[13];
+    if (grid_reduce<13>(acc, slot, tot) && threadIdx.x == 0) {
+      st->r_fwd[0] = tot[0];
+      st->r_fwd[1] = tot[1];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) st->r_step[k] = tot[2 + k];
+      st->r_step[4] = tot[6];
+      st->r_fwd2[0] = tot[7];
+      st->r_fwd2[1] = tot[8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) st->r_step2[k] = tot[9 + k];
+      ctrl_trial2(st, tot);
+    }
+    return;
   }
   // slot 5: GPBB ||x - P(x - theta g)||^2, or UPN ||x+ - x||^2; slot 8: TV_tau(xbar)
   FF acc[9] = {a0, a1, s0, s1, s2, s3, au, sb, sh};
@@ -645,6 +721,9 @@ void kernel_grids(Workspace &ws, int device, int64_t m, int64_t N) {
   ws.grid_trial_x = cap(
       occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_X, false>, TVR_BLOCK, device),
       fwd_need);
+  ws.grid_trial_2 = cap(
+      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_2, false>, TVR_BLOCK, device),
+      fwd_need);
   ws.grid_bwd = cap(
       occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device),
       cols);
@@ -749,8 +828,13 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
              ws.bwd, nullptr, nullptr, st, slot(1), nullptr, nullptr);
   mark(1, 1);
   mark(0, 0);
-  launch_pdl(solver == SOLVER_UPN ? fwd_kernel<FWD_TRIAL_X>(A) : fwd_kernel<FWD_TRIAL>(A),
-             solver == SOLVER_UPN ? ws.grid_trial_x : ws.grid_fwd, s, A, nullptr, nullptr, nullptr,
-             ws.fwd, st, slot(0), nullptr);
+  // `solver` is the pass kind: a solver, or PASS_GPBB2 (two trial points)
+  auto trial = solver == SOLVER_UPN   ? fwd_kernel<FWD_TRIAL_X>(A)
+               : solver == PASS_GPBB2 ? fwd_kernel<FWD_TRIAL_2>(A)
+                                      : fwd_kernel<FWD_TRIAL>(A);
+  const int grid = solver == SOLVER_UPN   ? ws.grid_trial_x
+                   : solver == PASS_GPBB2 ? ws.grid_trial_2
+                                          : ws.grid_fwd;
+  launch_pdl(trial, grid, s, A, nullptr, nullptr, nullptr, ws.fwd, st, slot(0), nullptr);
   mark(0, 1);
 }

@@ -52,6 +52,7 @@ bool pass_kind(int k, int solver) {
 // A batch of passes captured once per (system, method, batch size) and
 // replayed.  With kernel timing on, the graph also holds an event node pair
 // around every kernel and gives each pass its slot for the "did work" flags.
+// `solver` is the pass kind (a solver, or PASS_GPBB2).
 int pass_graph(tvr_system *sys, int solver, int batch, bool timed, cudaGraphExec_t *out) {
   cudaGraphExec_t &cache = timed ? sys->pass_graph_prof[solver] : sys->pass_graph[solver];
   int &cache_batch = timed ? sys->pass_graph_prof_batch[solver] : sys->pass_graph_batch[solver];
@@ -140,6 +141,7 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 struct Job {
   tvr_system *sys = nullptr;
   int solver = 0;
+  int pass = 0;  // solver, or PASS_GPBB2
   double alpha = 0, tau = 0, eps = 0;
   tvr_solve_opts o{};
   float *x = nullptr;
@@ -159,7 +161,7 @@ int check_opts(const tvr_solve_opts &o) {
       !finite_pos(o.L_bar) || !(o.mu_bar >= 0.0) || !std::isfinite(o.mu_bar) ||
       !(o.gpbb_sigma > 0.0 && o.gpbb_sigma < 1.0) || !(o.gpbb_beta0 > 0.0 && o.gpbb_beta0 < 1.0) ||
       (o.stop_mode != TVR_STOP_REL && o.stop_mode != TVR_STOP_PER_N) || o.history_len < 0 ||
-      (o.history_len > 0 && !o.history))
+      (o.history_len > 0 && !o.history) || o.gpbb_points < 0 || o.gpbb_points > 2)
     return fail(TVR_ERR_ARG, "tvr_solve: invalid options");
   return TVR_OK;
 }
@@ -181,6 +183,7 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   if (uo) j.o = *uo;
   if (int rc = check_opts(j.o)) return rc;
   const tvr_solve_opts &o = j.o;
+  j.pass = solver == SOLVER_GPBB && o.gpbb_points != 1 ? PASS_GPBB2 : solver;
   j.hist_n = o.history ? (o.history_len < (1 << 30) ? o.history_len : (1 << 30)) : 0;
   if (int rc = ensure_solver(sys, j.hist_n)) return rc;
   if (int rc = stage_in(b, sys->m, &sys->stage_bM, s, &j.bd)) return rc;
@@ -216,6 +219,7 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   h.pg = sys->pg;
   h.w = sys->wplanes[0];
   h.wt = sys->wplanes[1];
+  h.wt2 = sys->wplanes[2];
   h.hist = j.hist_n > 0 ? sys->hist_dev : nullptr;
   h.prof_flags = sys->prof_flags_dev;
   h.hist_cap = (int)j.hist_n;
@@ -225,7 +229,7 @@ int job_begin(Job &j, tvr_system *sys, int solver, const float *b, double alpha,
   j.exec = nullptr;
   j.timed_graph = o.use_graph && sys->profile && o.batch <= kProfPairs;
   if (o.use_graph && (!sys->profile || j.timed_graph))
-    if (int rc = pass_graph(sys, solver, o.batch, j.timed_graph, &j.exec)) return rc;
+    if (int rc = pass_graph(sys, j.pass, o.batch, j.timed_graph, &j.exec)) return rc;
   const int64_t trials = (o.bt_max > o.gpbb_max_trials ? o.bt_max : o.gpbb_max_trials) + 2;
   j.max_passes = ((int64_t)o.k_max + 1) * trials + o.batch;
   j.passes = 0;
@@ -257,7 +261,7 @@ int job_launch(Job &j) {
         }
         tp = &tm;
       }
-      launch_solver_pass(A, sys->st, j.solver, sys->ws, j.s, tp);
+      launch_solver_pass(A, sys->st, j.pass, sys->ws, j.s, tp);
     }
     TVR_CUDA(cudaGetLastError());
   }

@@ -40,18 +40,18 @@ struct tvr_system {
   float *vN[RN_COUNT] = {};
   float *vM[RM_COUNT] = {};
   float2 *pg = nullptr;
-  float *wplanes[2] = {nullptr, nullptr};  // Huber weight planes (4 N floats each)
+  float *wplanes[3] = {nullptr, nullptr, nullptr};  // Huber weight planes (4 N floats each)
   double *hist_dev = nullptr;
   int hist_cap = 0;
   int *pinned_flag = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t run_stream = nullptr;  // stream of this system's solve inside a batch
-  cudaGraphExec_t pass_graph[4] = {};
-  int pass_graph_batch[4] = {};
+  cudaGraphExec_t pass_graph[PASS_KINDS] = {};
+  int pass_graph_batch[PASS_KINDS] = {};
   // the same pass graphs with event nodes around every kernel (kernel timing)
-  cudaGraphExec_t pass_graph_prof[4] = {};
-  int pass_graph_prof_batch[4] = {};
-  int pass_graph_prof_mask[4] = {};  // profile | prof_stride << 8 the graph was captured with
+  cudaGraphExec_t pass_graph_prof[PASS_KINDS] = {};
+  int pass_graph_prof_batch[PASS_KINDS] = {};
+  int pass_graph_prof_mask[PASS_KINDS] = {};  // profile | prof_stride << 8 the graph was captured with
   cudaEvent_t *gprof_ev = nullptr;  // [gprof_batch][TVR_PROF_KINDS][2]
   int gprof_batch = 0;
   // kernel timing: event pairs of launches not yet harvested; a pair counts

@@ -282,16 +282,20 @@ __device__ __forceinline__ float huber_bregman(const float z[3], float nz, const
 // Vector roles are pointers that the control logic swaps on acceptance.
 // ---------------------------------------------------------------------------
 enum SolverKind { SOLVER_NONE = 0, SOLVER_GP = 1, SOLVER_GPBB = 2, SOLVER_UPN = 3 };
+// Kind of solver pass (graph cache slot): the solver, or GPBB with two trial
+// points per forward pass.
+enum { PASS_GPBB2 = 4, PASS_KINDS = 5 };
 
 // Y2, RY2, U2, RYS2: UPN's extrapolation formed speculatively by each trial
 // (the values y, A y - b, u would take if the trial is accepted); they swap
 // with Y, RY, U, RYS on acceptance.
-enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_Y2, RN_COUNT };
+// T2, RT2, RTS2: GPBB's second trial point of a pass (step beta^2 theta).
+enum RoleN { RN_X = 0, RN_T, RN_Y, RN_G, RN_GN, RN_Y2, RN_T2, RN_COUNT };
 // RS, RTS, RYS: the residuals R, RT, RY times the per-row scales (BF16 storage
 // only), which the back projection gathers so that it applies the same
 // matrix s_i q_ij as the forward projection.
-enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_RY2, RM_U2, RM_RS, RM_RTS, RM_RYS, RM_RYS2,
-             RM_COUNT };
+enum RoleM { RM_R = 0, RM_RT, RM_RY, RM_U, RM_AD, RM_RY2, RM_U2, RM_RT2, RM_RS, RM_RTS, RM_RYS,
+             RM_RYS2, RM_RTS2, RM_COUNT };
 
 #define TVR_FHIST 16
 
@@ -319,6 +323,9 @@ struct DevState {
   // on acceptance.
   int spec_upn;
   double r_spec[3];
+  // GPBB with two trial points per pass: the second point's sums
+  // {||A xbar2 - b||^2, ||A d2||^2} and {g^T d2, ||d2||^2, sum B_h, TV_tau(xbar2)}
+  double r_fwd2[2], r_step2[4];
   // vector roles
   float *vN[RN_COUNT];
   float *vM[RM_COUNT];
@@ -330,7 +337,7 @@ struct DevState {
   // its acceptance would make the next gradient point (xbar for GP / GPBB, y
   // for UPN), and the two swap on acceptance.  The back projection then reads
   // the TV gradient instead of re-evaluating the stencil.
-  float *w, *wt;
+  float *w, *wt, *wt2;  // wt2: planes at GPBB's second trial point
   // history (device buffer of hist_cap records)
   double *hist;
   int hist_cap, hist_used;
@@ -434,7 +441,7 @@ __device__ __forceinline__ void voxel_of(const MatDev &A, int64_t j, int &ix, in
 
 struct Workspace {
   RedSlot fwd, bwd, step, yf, tv, gmap;
-  int grid_fwd, grid_bwd, grid_elem, grid_trial_x;
+  int grid_fwd, grid_bwd, grid_elem, grid_trial_x, grid_trial_2;
 };
 
 // Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from

@@ -37,6 +37,8 @@ def geometries():
     out.append(("wide_det_misses", synth.cone_geometry(6, 4, 40, 18.0, 12.0, det_rows=3)))
     dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, 1, 1], [0.3, -0.7, 0.2]])
     out.append(("parallel_axes_diag", synth.parallel_geometry(6, dirs, 9)))
+    # the paper's scan shape at small size: 19 directions spread over the sphere
+    out.append(("sphere19", synth.sphere_parallel_geometry(8, 19, 13)))
     return out
 
 

@@ -216,3 +216,16 @@ def test_small_grids_of_odd_and_even_edge(n, method):
     _, spread = oracle_spread(prob, ORACLE[method], 1e-4, draws=2)
     d = rel_l2(x.cpu().numpy(), ref.x)
     assert d <= max(XSTAR_TOL, 3 * spread), (d, spread)
+
+
+def test_gpbb_two_points_per_pass_give_the_same_iterates(c32):
+    """Forming the post-rejection trial in the same pass changes only how many
+    passes run: the decisions, counts and iterates are those of one point per
+    pass, bit for bit."""
+    r1, x1 = gpu_solve(c32, "gpbb", gpbb_points=1, batch=1)
+    r2, x2 = gpu_solve(c32, "gpbb", gpbb_points=2, batch=1)
+    assert (r1.status, r1.iters, r1.f_evals, r1.g_evals, r1.trials) == \
+           (r2.status, r2.iters, r2.f_evals, r2.g_evals, r2.trials)
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(r1.history, r2.history)
+    assert r1.trials > 0 and r2.passes < r1.passes
