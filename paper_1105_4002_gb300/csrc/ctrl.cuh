@@ -5,7 +5,7 @@
 // A solver pass is two kernels: the back projection (gradient at the newly
 // accepted point, then ctrl_after_grad) and the trial kernel (projected step,
 // forward projection, in UPN the extrapolation for the case of acceptance,
-// then ctrl_trial).
+// then ctrl_trial, or ctrl_trial2 for GPBB's two trial points).
 //
 // The acceptance tests are evaluated in Bregman form.  For f = phi and a step
 // d = xbar - p from a base point p with gradient g = grad f(p),

@@ -6,7 +6,9 @@
 //               the projected step over the voxels (g^T d, ||d||^2, sum_j B_h,
 //               TV_tau(xbar), the Huber weights of the next gradient point) and,
 //               in UPN, the extrapolation y = x+ + beta (x+ - x) with its residual
-//               A y - b for the case of acceptance; the last block runs the test
+//               A y - b for the case of acceptance; GPBB forms two trial points
+//               (the second at the step a rejection leads to); the last block
+//               runs the test
 //   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free); plain
 //               modes fuse the TV_tau stencil and its value, the solver mode
 //               reads the TV gradient from the Huber weight planes and adds the
