@@ -399,6 +399,26 @@ def run_paper(args):
 
 
 # ------------------------------------------------------------- batching
+def solver_launch_bytes(m: int, N: int, nnz: int, storage: str, method: str):
+    """Algorithmic bytes of one working launch of the solver's two kernels,
+    (back projection, trial), each stream counted once: int32 indices, int64
+    pointers, float32 values (or bfloat16 plus a float32 scale per row and a
+    scaled residual)."""
+    vb = 4 if storage == "fp32" else 2
+    extra_m = 0 if storage == "fp32" else 8
+    # back projection: A^T (values + indices), column pointers, r gather, the
+    # four Huber weight planes, x read and g and (p, g) written
+    bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
+    # trial: A (values + indices), row pointers, the (p, g) pairs read and xbar
+    # written, b read and r written; GPBB (two points per pass) writes the four
+    # Huber weight planes at both points and the second point's xbar and
+    # residual; UPN reads u and x and writes u, A y - b, y and the planes at y
+    # (the extrapolation for the case of acceptance); GP writes the planes at xbar
+    fwd = (4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
+    fwd += {"gpbb": 16 * N + 4 * m + 20 * N, "upn": 12 * m + 24 * N, "gp": 16 * N}[method]
+    return bwd, fwd
+
+
 def batch_problems(count=48, seed=5):
     """Uneven problems: edge U{24..96}, views U{8..40}, detector 1.5 x edge (seeded)."""
     import numpy as np
@@ -456,8 +476,15 @@ def run_batch(args):
             s_.solve("upn", b, alpha, tau, eps, x.zero_())
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
+        moved = 0.0
+        for s_, r in zip(systems, rb):
+            bb, bf = solver_launch_bytes(s_.m, s_.N, s_.nnz, storage, "upn")
+            moved += r.g_evals * bb + r.trials * bf
+        peak, _ = measured_peak_gbs()
         res[f"batch48_{storage}"] = {
             "solves_per_s": len(systems) / t_batch, "ms": 1e3 * t_batch,
+            "algorithmic_gb": moved / 1e9, "achieved_gbs": moved / t_batch / 1e9,
+            "frac_of_measured_hbm": moved / t_batch / 1e9 / peak,
             "one_by_one_solves_per_s": len(systems) / t_seq,
             "converged": sum(r.status == 0 for r in rb), "iters_total": sum(r.iters for r in rb)}
         del systems, bs, xs
@@ -673,22 +700,10 @@ def main():
         return
 
     m, N, nnz = geom.m, geom.N, sysm.nnz
-    # algorithmic bytes per launch (solver mode; int32 indices, int64 pointers, values float32,
-    # or bfloat16 plus a float32 scale per row and a scaled residual)
-    vb = 4 if args.storage == "fp32" else 2
-    extra_m = 0 if args.storage == "fp32" else 8
-    # solver back projection: A^T (values + indices), column pointers, r gather,
-    # the four Huber weight planes, x read and g and (p, g) written
-    bytes_bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
-    # trial kernel: A (values + indices), row pointers, the (p, g) pairs read and
-    # xbar written, b read and r written; GPBB trials (two points per pass)
-    # write the four Huber weight planes at both points and the second point's
-    # xbar and residual; UPN trials read u and x and write u, A y - b, y and
-    # the planes at y (the extrapolation for the case of acceptance).  Weighted
-    # by the share of each method's trial launches among the timed launches.
     w_share = passes_gpbb / max(passes_gpbb + passes_upn, 1)
-    bytes_fwd = ((4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
-                 + w_share * (16 * N + 4 * m + 20 * N) + (1 - w_share) * (12 * m + 24 * N))
+    bytes_bwd, fwd_g = solver_launch_bytes(m, N, nnz, args.storage, "gpbb")
+    _, fwd_u = solver_launch_bytes(m, N, nnz, args.storage, "upn")
+    bytes_fwd = w_share * fwd_g + (1 - w_share) * fwd_u
     # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
     t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage)
     t_u = captured_traffic("fwd_csr_trial_upn", args.storage)

@@ -1,8 +1,10 @@
 // GP / GPBB / UPN drivers.
 //
 // A solve is a sequence of identical "passes" (kernels.cu, launch_solver_pass):
-//   [UPN: y-extrapolation] -> gradient at the newly accepted point
-//   -> projected trial step -> forward projection + acceptance test.
+//   gradient at the newly accepted point (back projection)
+//   -> trial kernel (projected step, forward projection, acceptance test;
+//      UPN's extrapolation for the case of acceptance, or GPBB's second
+//      trial point).
 // Kernels whose work is not due (no new point yet, or the solve has stopped)
 // return at once after reading the device state, so the host never needs to
 // know the outcome of a line-search trial: it launches passes in batches --
@@ -14,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "system.cuh"
@@ -383,21 +386,30 @@ int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t method,
                            sys->run_stream))
       return rc;
   }
-  // interleave: every unfinished problem gets a batch of passes on its own
-  // stream, then the host reads all flags
-  for (;;) {
-    bool all = true;
-    for (auto &j : jobs)
-      if (!j.done) {
-        if (int rc = job_launch(j)) return rc;
-        all = false;
+  // Every problem runs batches of passes on its own stream; the host relaunches
+  // each one as soon as its previous batch has drained, so small problems do
+  // not wait for the large ones.
+  for (auto &j : jobs)
+    if (int rc = job_launch(j)) return rc;
+  for (int running = count; running > 0;) {
+    bool progressed = false;
+    for (auto &j : jobs) {
+      if (j.done) continue;
+      const cudaError_t q = cudaStreamQuery(j.s);
+      if (q == cudaErrorNotReady) {
+        // not an error: keep it out of the error checks that follow launches
+        if (cudaPeekAtLastError() == cudaErrorNotReady) (void)cudaGetLastError();
+        continue;
       }
-    if (all) break;
-    for (auto &j : jobs)
-      if (!j.done) {
-        TVR_CUDA(cudaStreamSynchronize(j.s));
-        if (int rc = job_poll(j)) return rc;
-      }
+      if (q != cudaSuccess) return cuda_fail(q, "cudaStreamQuery(solve batch)");
+      progressed = true;
+      if (int rc = job_poll(j)) return rc;
+      if (j.done)
+        --running;
+      else if (int rc = job_launch(j))
+        return rc;
+    }
+    if (!progressed) std::this_thread::yield();
   }
   int worst = TVR_OK;
   for (int i = 0; i < count; ++i) {

@@ -1,5 +1,6 @@
-"""Batch of independent uneven problems (batching pattern): interleaved on
-their own streams, each must give exactly the result of solving it alone."""
+"""Batch of independent uneven problems (batching pattern): side by side on
+their own streams (each relaunched as soon as its previous batch of passes
+drains), each must give exactly the result of solving it alone."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,7 @@ def problems():
     return out
 
 
-@pytest.mark.parametrize("method", ["upn", "gpbb"])
+@pytest.mark.parametrize("method", ["upn", "gpbb", "gp"])
 def test_batch_equals_single_solves(method):
     torch = cuda()
     from paper_1105_4002_gb300 import System, solve_batch
