@@ -407,8 +407,11 @@ def solver_launch_bytes(m: int, N: int, nnz: int, storage: str, method: str):
     vb = 4 if storage == "fp32" else 2
     extra_m = 0 if storage == "fp32" else 8
     # back projection: A^T (values + indices), column pointers, r gather, the
-    # four Huber weight planes, x read and g and (p, g) written
+    # four Huber weight planes, x read and g and (p, g) written; GPBB also
+    # reads x and g of the previous iterate for the BB dots
     bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 16 * N + 4 * N + 4 * N + 8 * N
+    if method == "gpbb":
+        bwd += 8 * N
     # trial: A (values + indices), row pointers, the (p, g) pairs read and xbar
     # written, b read and r written; GPBB (two points per pass) writes the four
     # Huber weight planes at both points and the second point's xbar and
@@ -417,6 +420,17 @@ def solver_launch_bytes(m: int, N: int, nnz: int, storage: str, method: str):
     fwd = (4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
     fwd += {"gpbb": 16 * N + 4 * m + 20 * N, "upn": 12 * m + 24 * N, "gp": 16 * N}[method]
     return bwd, fwd
+
+
+def plain_launch_bytes(m: int, N: int, nnz: int, storage: str):
+    """Algorithmic bytes of the plain phi + grad phi kernels, (forward, back
+    projection): r = A x - b with x gathered and b read, r written; g = A^T r +
+    alpha grad TV with r gathered, x read (TV stencil) and g written."""
+    vb = 4 if storage == "fp32" else 2
+    extra_m = 0 if storage == "fp32" else 8
+    fwd = (4 + vb) * nnz + 8 * (m + 1) + 4 * N + 8 * m + extra_m * m
+    bwd = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 8 * N
+    return fwd, bwd
 
 
 def batch_problems(count=48, seed=5):
@@ -701,9 +715,10 @@ def main():
 
     m, N, nnz = geom.m, geom.N, sysm.nnz
     w_share = passes_gpbb / max(passes_gpbb + passes_upn, 1)
-    bytes_bwd, fwd_g = solver_launch_bytes(m, N, nnz, args.storage, "gpbb")
-    _, fwd_u = solver_launch_bytes(m, N, nnz, args.storage, "upn")
+    bwd_g, fwd_g = solver_launch_bytes(m, N, nnz, args.storage, "gpbb")
+    bwd_u, fwd_u = solver_launch_bytes(m, N, nnz, args.storage, "upn")
     bytes_fwd = w_share * fwd_g + (1 - w_share) * fwd_u
+    bytes_bwd = w_share * bwd_g + (1 - w_share) * bwd_u
     # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
     t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage)
     t_u = captured_traffic("fwd_csr_trial_upn", args.storage)
@@ -728,8 +743,7 @@ def main():
                                   "(event nodes around each kernel slow the small ones); the "
                                   "projected step runs inside the trial forward kernel"}
     pf, pb = phi_prof["forward"], phi_prof["backward"]
-    plain_f = (4 + vb) * nnz + 8 * (m + 1) + 4 * N + 8 * m + extra_m * m
-    plain_b = (4 + vb) * nnz + 8 * (N + 1) + 4 * m + 8 * N
+    plain_f, plain_b = plain_launch_bytes(m, N, nnz, args.storage)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,

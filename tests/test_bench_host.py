@@ -1,0 +1,52 @@
+"""Host-side pieces of bench.py, on the CPU: the algorithmic-bytes model of
+each kernel (against the counts of the 64^3 bench problem: m = 230,400 rays,
+N = 64^3 voxels, nnz = 19,477,604) and a static check that every name the
+bench's functions read is defined (the GPU paths do not run here)."""
+import builtins
+import os
+import symtable
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+M, N, NNZ = 230_400, 64 ** 3, 19_477_604
+
+
+def test_plain_kernel_bytes():
+    f, b = bench.plain_launch_bytes(M, N, NNZ, "fp32")
+    # forward: 8 B per entry, 8 B per row pointer, x gathered once, b read, r written
+    assert f == 8 * NNZ + 8 * (M + 1) + 4 * N + 8 * M
+    assert b == 8 * NNZ + 8 * (N + 1) + 4 * M + 8 * N
+    assert round(f / 1e6, 1) == 160.6 and round(b / 1e6, 1) == 160.9
+    f16, b16 = bench.plain_launch_bytes(M, N, NNZ, "bf16")
+    # bfloat16 values: 2 B less per entry, plus the row scale and the scaled residual
+    assert f - f16 == 2 * NNZ - 8 * M and b - b16 == 2 * NNZ
+
+
+@pytest.mark.parametrize("method,bwd,fwd", [("gpbb", 169.3, 173.0), ("upn", 167.2, 171.7),
+                                            ("gp", 167.2, 166.8)])
+def test_solver_kernel_bytes(method, bwd, fwd):
+    b, f = bench.solver_launch_bytes(M, N, NNZ, "fp32", method)
+    assert (round(b / 1e6, 1), round(f / 1e6, 1)) == (bwd, fwd)
+
+
+def _free_globals(table, out):
+    for sym in table.get_symbols():
+        if sym.is_global() and sym.is_referenced() and not sym.is_assigned():
+            out.add(sym.get_name())
+    for child in table.get_children():
+        _free_globals(child, out)
+
+
+def test_bench_reads_no_undefined_name():
+    path = os.path.join(ROOT, "bench.py")
+    src = open(path).read()
+    top = symtable.symtable(src, path, "exec")
+    defined = {s.get_name() for s in top.get_symbols() if s.is_assigned() or s.is_imported()}
+    free = set()
+    for child in top.get_children():
+        _free_globals(child, free)
+    missing = sorted(n for n in free if n not in defined and not hasattr(builtins, n))
+    assert not missing, missing
