@@ -208,150 +208,144 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
   const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
   FF a0 = ff_zero(), a1 = ff_zero(), au = ff_zero();
   FF c0 = ff_zero(), c1 = ff_zero();  // two-point trial: the second point's residual sums
-  for (int64_t base = warp * RPW; base < A.m; base += nwarp * RPW) {
-    const int64_t row = base + sub;
-    const bool valid = row < A.m;
-    int64_t beg = 0, end = 0;
-    if (valid && !MF) {
-      beg = __ldg(A.row_ptr + row);
-      end = __ldg(A.row_ptr + row + 1);
-    }
-    float sx = 0.f, sd = 0.f, sx2 = 0.f, sd2 = 0.f;
-    if (MF && valid) {
-      // matrix-free: the entries of the row from the ray geometry (mf.cuh)
-      const int64_t per = (int64_t)A.Pu * A.Pv;
-      const int vi = (int)(row / per);
-      const int64_t rem = row - (int64_t)vi * per;
-      const int q = (int)(rem / A.Pu), pp = (int)(rem - (int64_t)q * A.Pu);
-      MfRay ray;
-      mf_pixel_ray(A.mfv[vi], A.kind, A.Pu, A.Pv, pp, q, ray);
-      mf_row<G>(ray, A.n, lane, [&](int c, float v) {
+  auto rows_phase = [&]() {
+    for (int64_t base = warp * RPW; base < A.m; base += nwarp * RPW) {
+      const int64_t row = base + sub;
+      const bool valid = row < A.m;
+      int64_t beg = 0, end = 0;
+      if (valid && !MF) {
+        beg = __ldg(A.row_ptr + row);
+        end = __ldg(A.row_ptr + row + 1);
+      }
+      float sx = 0.f, sd = 0.f, sx2 = 0.f, sd2 = 0.f;
+      if (MF && valid) {
+        // matrix-free: the entries of the row from the ray geometry (mf.cuh)
+        const int64_t per = (int64_t)A.Pu * A.Pv;
+        const int vi = (int)(row / per);
+        const int64_t rem = row - (int64_t)vi * per;
+        const int q = (int)(rem / A.Pu), pp = (int)(rem - (int64_t)q * A.Pu);
+        MfRay ray;
+        mf_pixel_ray(A.mfv[vi], A.kind, A.Pu, A.Pv, pp, q, ray);
+        mf_row<G>(ray, A.n, lane, [&](int c, float v) {
+          if (TRIAL) {
+            const float2 qc = __ldg(pg + c);
+            const float bc = xbar_of(qc.x, qc.y, s);
+            sx = __fmaf_rn(v, bc, sx);
+            sd = __fmaf_rn(v, __fsub_rn(bc, qc.x), sd);
+            if (TWO) {
+              const float bc2 = xbar_of(qc.x, qc.y, sq);
+              sx2 = __fmaf_rn(v, bc2, sx2);
+              sd2 = __fmaf_rn(v, __fsub_rn(bc2, qc.x), sd2);
+            }
+          } else {
+            sx = __fmaf_rn(v, __ldg(x + c), sx);
+          }
+        });
+      }
+      // Rows are padded to multiples of 4 entries: each lane reads 4 entries
+      // with one 16-byte load of indices and one of values, then gathers.  The
+      // loads of the lane's next 4 entries are issued before this trip's
+      // arithmetic waits on its gathers (a two-stage software pipeline).
+      int64_t e0 = beg + 4 * lane;
+      int4 cn = make_int4(0, 0, 0, 0);
+      float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e0 < end) {
+        cn = ld_stream(A.col + e0);
+        vn = load4<BF>(A.val, A.qval, e0);
+      }
+      for (; e0 < end; e0 += 4 * G) {
+        const int4 c4 = cn;
+        const float4 v4 = vn;
+        const int64_t e1 = e0 + 4 * G;
         if (TRIAL) {
-          const float2 qc = __ldg(pg + c);
-          const float bc = xbar_of(qc.x, qc.y, s);
-          sx = __fmaf_rn(v, bc, sx);
-          sd = __fmaf_rn(v, __fsub_rn(bc, qc.x), sd);
-          if (TWO) {
-            const float bc2 = xbar_of(qc.x, qc.y, sq);
-            sx2 = __fmaf_rn(v, bc2, sx2);
-            sd2 = __fmaf_rn(v, __fsub_rn(bc2, qc.x), sd2);
+          // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
+          const float2 q0 = __ldg(pg + c4.x), q1 = __ldg(pg + c4.y);
+          const float2 q2 = __ldg(pg + c4.z), q3 = __ldg(pg + c4.w);
+          if (e1 < end) {
+            cn = ld_stream(A.col + e1);
+            vn = load4<BF>(A.val, A.qval, e1);
+          }
+          const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
+          const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
+          sx = __fmaf_rn(v4.x, b0, sx);
+          sd = __fmaf_rn(v4.x, __fsub_rn(b0, q0.x), sd);
+          sx = __fmaf_rn(v4.y, b1, sx);
+          sd = __fmaf_rn(v4.y, __fsub_rn(b1, q1.x), sd);
+          sx = __fmaf_rn(v4.z, b2, sx);
+          sd = __fmaf_rn(v4.z, __fsub_rn(b2, q2.x), sd);
+          sx = __fmaf_rn(v4.w, b3, sx);
+          sd = __fmaf_rn(v4.w, __fsub_rn(b3, q3.x), sd);
+          if (TWO) {  // the second point, from the same gathered pairs
+            const float e0_ = xbar_of(q0.x, q0.y, sq), e1_ = xbar_of(q1.x, q1.y, sq);
+            const float e2_ = xbar_of(q2.x, q2.y, sq), e3_ = xbar_of(q3.x, q3.y, sq);
+            sx2 = __fmaf_rn(v4.x, e0_, sx2);
+            sd2 = __fmaf_rn(v4.x, __fsub_rn(e0_, q0.x), sd2);
+            sx2 = __fmaf_rn(v4.y, e1_, sx2);
+            sd2 = __fmaf_rn(v4.y, __fsub_rn(e1_, q1.x), sd2);
+            sx2 = __fmaf_rn(v4.z, e2_, sx2);
+            sd2 = __fmaf_rn(v4.z, __fsub_rn(e2_, q2.x), sd2);
+            sx2 = __fmaf_rn(v4.w, e3_, sx2);
+            sd2 = __fmaf_rn(v4.w, __fsub_rn(e3_, q3.x), sd2);
           }
         } else {
-          sx = __fmaf_rn(v, __ldg(x + c), sx);
-        }
-      });
-    }
-    // Rows are padded to multiples of 4 entries: each lane reads 4 entries
-    // with one 16-byte load of indices and one of values, then gathers.  The
-    // loads of the lane's next 4 entries are issued before this trip's
-    // arithmetic waits on its gathers (a two-stage software pipeline).
-    int64_t e0 = beg + 4 * lane;
-    int4 cn = make_int4(0, 0, 0, 0);
-    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e0 < end) {
-      cn = ld_stream(A.col + e0);
-      vn = load4<BF>(A.val, A.qval, e0);
-    }
-    for (; e0 < end; e0 += 4 * G) {
-      const int4 c4 = cn;
-      const float4 v4 = vn;
-      const int64_t e1 = e0 + 4 * G;
-      if (TRIAL) {
-        // xbar_j = P_Q(p_j - s g_j) and d_j = xbar_j - p_j, as the step phase forms them
-        const float2 q0 = __ldg(pg + c4.x), q1 = __ldg(pg + c4.y);
-        const float2 q2 = __ldg(pg + c4.z), q3 = __ldg(pg + c4.w);
-        if (e1 < end) {
-          cn = ld_stream(A.col + e1);
-          vn = load4<BF>(A.val, A.qval, e1);
-        }
-        const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
-        const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
-        sx = __fmaf_rn(v4.x, b0, sx);
-        sd = __fmaf_rn(v4.x, __fsub_rn(b0, q0.x), sd);
-        sx = __fmaf_rn(v4.y, b1, sx);
-        sd = __fmaf_rn(v4.y, __fsub_rn(b1, q1.x), sd);
-        sx = __fmaf_rn(v4.z, b2, sx);
-        sd = __fmaf_rn(v4.z, __fsub_rn(b2, q2.x), sd);
-        sx = __fmaf_rn(v4.w, b3, sx);
-        sd = __fmaf_rn(v4.w, __fsub_rn(b3, q3.x), sd);
-        if (TWO) {  // the second point, from the same gathered pairs
-          const float e0_ = xbar_of(q0.x, q0.y, sq), e1_ = xbar_of(q1.x, q1.y, sq);
-          const float e2_ = xbar_of(q2.x, q2.y, sq), e3_ = xbar_of(q3.x, q3.y, sq);
-          sx2 = __fmaf_rn(v4.x, e0_, sx2);
-          sd2 = __fmaf_rn(v4.x, __fsub_rn(e0_, q0.x), sd2);
-          sx2 = __fmaf_rn(v4.y, e1_, sx2);
-          sd2 = __fmaf_rn(v4.y, __fsub_rn(e1_, q1.x), sd2);
-          sx2 = __fmaf_rn(v4.z, e2_, sx2);
-          sd2 = __fmaf_rn(v4.z, __fsub_rn(e2_, q2.x), sd2);
-          sx2 = __fmaf_rn(v4.w, e3_, sx2);
-          sd2 = __fmaf_rn(v4.w, __fsub_rn(e3_, q3.x), sd2);
-        }
-      } else {
-        const float x0 = __ldg(x + c4.x), x1 = __ldg(x + c4.y);
-        const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
-        if (e1 < end) {
-          cn = ld_stream(A.col + e1);
-          vn = load4<BF>(A.val, A.qval, e1);
-        }
-        sx = __fmaf_rn(v4.x, x0, sx);
-        sx = __fmaf_rn(v4.y, x1, sx);
-        sx = __fmaf_rn(v4.z, x2, sx);
-        sx = __fmaf_rn(v4.w, x3, sx);
-      }
-    }
-    sx = group_sum<G>(sx);
-    if (TRIAL) sd = group_sum<G>(sd);
-    if (TWO) {
-      sx2 = group_sum<G>(sx2);
-      sd2 = group_sum<G>(sd2);
-    }
-    if (valid && lane == 0) {
-      float sc = 1.f;
-      if (BF) {
-        sc = __ldg(A.rscale + row);
-        sx = __fmul_rn(sc, sx);
-        sd = __fmul_rn(sc, sd);
-        if (TWO) {
-          sx2 = __fmul_rn(sc, sx2);
-          sd2 = __fmul_rn(sc, sd2);
+          const float x0 = __ldg(x + c4.x), x1 = __ldg(x + c4.y);
+          const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
+          if (e1 < end) {
+            cn = ld_stream(A.col + e1);
+            vn = load4<BF>(A.val, A.qval, e1);
+          }
+          sx = __fmaf_rn(v4.x, x0, sx);
+          sx = __fmaf_rn(v4.y, x1, sx);
+          sx = __fmaf_rn(v4.z, x2, sx);
+          sx = __fmaf_rn(v4.w, x3, sx);
         }
       }
-      if (MODE == FWD_Y) {
-        r[row] = sx;
-      } else {
-        const float ri = __fsub_rn(sx, __ldg(b + row));
-        r[row] = ri;
-        if (BF && rs) rs[row] = __fmul_rn(sc, ri);
-        ff_add_prod(a0, ri, ri);
-        if (TRIAL) {
-          ff_add_prod(a1, sd, sd);
+      sx = group_sum<G>(sx);
+      if (TRIAL) sd = group_sum<G>(sd);
+      if (TWO) {
+        sx2 = group_sum<G>(sx2);
+        sd2 = group_sum<G>(sd2);
+      }
+      if (valid && lane == 0) {
+        float sc = 1.f;
+        if (BF) {
+          sc = __ldg(A.rscale + row);
+          sx = __fmul_rn(sc, sx);
+          sd = __fmul_rn(sc, sd);
           if (TWO) {
-            const float ri2 = __fsub_rn(sx2, __ldg(b + row));
-            st->vM[RM_RT2][row] = ri2;
-            if (BF) st->vM[RM_RTS2][row] = __fmul_rn(sc, ri2);
-            ff_add_prod(c0, ri2, ri2);
-            ff_add_prod(c1, sd2, sd2);
+            sx2 = __fmul_rn(sc, sx2);
+            sd2 = __fmul_rn(sc, sd2);
           }
-          if (SPEC) {  // UPN: u and A y - b for the case of acceptance (residual by linearity)
-            const float un = __fmaf_rn(bcur, u_old[row], sd);
-            u2[row] = un;
-            const float ry = __fmaf_rn(bnew, un, ri);
-            ry2[row] = ry;
-            if (BF && rys2) rys2[row] = __fmul_rn(sc, ry);
-            ff_add_prod(au, un, un);
+        }
+        if (MODE == FWD_Y) {
+          r[row] = sx;
+        } else {
+          const float ri = __fsub_rn(sx, __ldg(b + row));
+          r[row] = ri;
+          if (BF && rs) rs[row] = __fmul_rn(sc, ri);
+          ff_add_prod(a0, ri, ri);
+          if (TRIAL) {
+            ff_add_prod(a1, sd, sd);
+            if (TWO) {
+              const float ri2 = __fsub_rn(sx2, __ldg(b + row));
+              st->vM[RM_RT2][row] = ri2;
+              if (BF) st->vM[RM_RTS2][row] = __fmul_rn(sc, ri2);
+              ff_add_prod(c0, ri2, ri2);
+              ff_add_prod(c1, sd2, sd2);
+            }
+            if (SPEC) {  // UPN: u and A y - b for the case of acceptance (residual by linearity)
+              const float un = __fmaf_rn(bcur, u_old[row], sd);
+              u2[row] = un;
+              const float ry = __fmaf_rn(bnew, un, ri);
+              ry2[row] = ry;
+              if (BF && rys2) rys2[row] = __fmul_rn(sc, ry);
+              ff_add_prod(au, un, un);
+            }
           }
         }
       }
     }
-  }
-  if (MODE == FWD_Y) return;
-  if (!TRIAL) {
-    FF acc[1] = {a0};
-    double tot[1];
-    if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0 && MODE == FWD_INIT)
-      st->r_init[0] = tot[0];
-    return;
-  }
+  };
   // Step phase: xbar = P_Q(p - s g) (eq. gradientmethod; Alg. 1, Alg. 2) over
   // the voxels, with the reductions of the acceptance tests.  xbar at the
   // forward neighbours is recomputed with the same expression, so the TV
@@ -364,69 +358,94 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
   FF sh = ff_zero();  // TV_tau(xbar)
   // two-point trial: the second point's g^T d, ||d||^2, sum B_h, TV_tau
   FF d0 = ff_zero(), d1 = ff_zero(), d2 = ff_zero(), dh = ff_zero();
-  {
-    const bool upn = st->solver == SOLVER_UPN;
-    constexpr bool spec = SPEC;
-    const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
-    const float sg2 = (float)st->step2;
-    const float tau = (float)st->tau;
-    float *__restrict__ t = st->vN[RN_T];
-    float *__restrict__ wt = (!upn || spec) ? st->wt : nullptr;
-    const float *__restrict__ xo = st->vN[RN_X];
-    float *__restrict__ y2 = st->vN[RN_Y2];
-    const int n = A.n;
-    const int64_t nn = (int64_t)n * n, N = A.N;
-    const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
-    for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < N; j += stride) {
-      const float2 q = pg[j];
-      const float xb = xbar_of(q.x, q.y, s);
-      int ix, iy, iz;
-      voxel_of(A, j, ix, iy, iz);
-      const int64_t off[3] = {1, n, nn};
-      const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
-      float pk[3], gk[3], xk[3];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const float2 qk = in[e] ? pg[j + off[e]] : make_float2(0.f, 0.f);
-        pk[e] = qk.x;
-        gk[e] = qk.y;
-        xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
-      }
-      float w[3];
-      step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, sh, w);
-      t[j] = xb;
-      if (TWO) {  // the second point, as a trial at step sq would form it
-        const float xq = xbar_of(q.x, q.y, sq);
-        float xkq[3], wq[3];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) xkq[e] = in[e] ? xbar_of(pk[e], gk[e], sq) : 0.f;
-        FF unused = ff_zero();
-        step_voxel(q.x, q.y, xq, pk, xkq, in, sg2, false, tau, d0, d1, d2, unused, dh, wq);
-        st->vN[RN_T2][j] = xq;
-        float *__restrict__ wq_ = st->wt2;
-        wq_[j] = wq[0];
-        wq_[N + j] = wq[1];
-        wq_[2 * N + j] = wq[2];
-        wq_[3 * N + j] = __fadd_rn(__fadd_rn(wq[0], wq[1]), wq[2]);
-      }
-      if (spec) {
-        const float xoj = xo[j];
-        const float dx = __fsub_rn(xb, xoj);
-        const float yj = __fmaf_rn(bnew, dx, xb);
-        ff_add_prod(s3, dx, dx);
-        float yk[3];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) yk[e] = in[e] ? y_of(xk[e], xo[j + off[e]], bnew) : 0.f;
-        yform_voxel(xb, yj, xk, yk, in, tau, sb, w);
-        y2[j] = yj;
-      }
-      if (wt) {  // Huber weights at the next gradient point: xbar (GP, GPBB) or y (UPN)
-        wt[j] = w[0];
-        wt[N + j] = w[1];
-        wt[2 * N + j] = w[2];
-        wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
+  auto voxel_phase = [&]() {
+    if constexpr (TRIAL) {
+      {
+        const bool upn = st->solver == SOLVER_UPN;
+        constexpr bool spec = SPEC;
+        const bool want_g2 = st->solver == SOLVER_GPBB && st->trial == 0;
+        const float sg2 = (float)st->step2;
+        const float tau = (float)st->tau;
+        float *__restrict__ t = st->vN[RN_T];
+        float *__restrict__ wt = (!upn || spec) ? st->wt : nullptr;
+        const float *__restrict__ xo = st->vN[RN_X];
+        float *__restrict__ y2 = st->vN[RN_Y2];
+        const int n = A.n;
+        const int64_t nn = (int64_t)n * n, N = A.N;
+        const int64_t stride = (int64_t)gridDim.x * TVR_BLOCK;
+        for (int64_t j = (int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x; j < N; j += stride) {
+          const float2 q = pg[j];
+          const float xb = xbar_of(q.x, q.y, s);
+          int ix, iy, iz;
+          voxel_of(A, j, ix, iy, iz);
+          const int64_t off[3] = {1, n, nn};
+          const bool in[3] = {ix + 1 < n, iy + 1 < n, iz + 1 < n};
+          float pk[3], gk[3], xk[3];
+    #pragma unroll
+          for (int e = 0; e < 3; ++e) {
+            const float2 qk = in[e] ? pg[j + off[e]] : make_float2(0.f, 0.f);
+            pk[e] = qk.x;
+            gk[e] = qk.y;
+            xk[e] = in[e] ? xbar_of(qk.x, qk.y, s) : 0.f;
+          }
+          float w[3];
+          step_voxel<!SPEC>(q.x, q.y, xb, pk, xk, in, sg2, want_g2, tau, s0, s1, s2, s3, sh, w);
+          t[j] = xb;
+          if (TWO) {  // the second point, as a trial at step sq would form it
+            const float xq = xbar_of(q.x, q.y, sq);
+            float xkq[3], wq[3];
+    #pragma unroll
+            for (int e = 0; e < 3; ++e) xkq[e] = in[e] ? xbar_of(pk[e], gk[e], sq) : 0.f;
+            FF unused = ff_zero();
+            step_voxel(q.x, q.y, xq, pk, xkq, in, sg2, false, tau, d0, d1, d2, unused, dh, wq);
+            st->vN[RN_T2][j] = xq;
+            float *__restrict__ wq_ = st->wt2;
+            wq_[j] = wq[0];
+            wq_[N + j] = wq[1];
+            wq_[2 * N + j] = wq[2];
+            wq_[3 * N + j] = __fadd_rn(__fadd_rn(wq[0], wq[1]), wq[2]);
+          }
+          if (spec) {
+            const float xoj = xo[j];
+            const float dx = __fsub_rn(xb, xoj);
+            const float yj = __fmaf_rn(bnew, dx, xb);
+            ff_add_prod(s3, dx, dx);
+            float yk[3];
+    #pragma unroll
+            for (int e = 0; e < 3; ++e) yk[e] = in[e] ? y_of(xk[e], xo[j + off[e]], bnew) : 0.f;
+            yform_voxel(xb, yj, xk, yk, in, tau, sb, w);
+            y2[j] = yj;
+          }
+          if (wt) {  // Huber weights at the next gradient point: xbar (GP, GPBB) or y (UPN)
+            wt[j] = w[0];
+            wt[N + j] = w[1];
+            wt[2 * N + j] = w[2];
+            wt[3 * N + j] = __fadd_rn(__fadd_rn(w[0], w[1]), w[2]);
+          }
+        }
       }
     }
+  };
+  // The two phases of a trial are independent (the rows gather (p, g) and
+  // write the residuals; the voxels read (p, g) and x and write xbar, y and
+  // the planes).  Odd warps run the voxels first, so that every SM mixes
+  // latency-bound voxel work with the row streams instead of ending the
+  // kernel on the voxel phase alone.
+  const bool voxels_first = TRIAL && (warp & 1);
+#pragma unroll 1
+  for (int ph = 0; ph < 2; ++ph) {
+    if ((ph == 0) != voxels_first)
+      rows_phase();
+    else
+      voxel_phase();
+  }
+  if (MODE == FWD_Y) return;
+  if (!TRIAL) {
+    FF acc[1] = {a0};
+    double tot[1];
+    if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0 && MODE == FWD_INIT)
+      st->r_init[0] = tot[0];
+    return;
   }
   if constexpr (TWO) {
     // {first point: ||r||^2, ||A d||^2, g^T d, ||d||^2, sum B_h, ||x - P(x - theta g)||^2,
