@@ -218,6 +218,10 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
         end = __ldg(A.row_ptr + row + 1);
       }
       float sx = 0.f, sd = 0.f, sx2 = 0.f, sd2 = 0.f;
+      // plain modes: b_i loaded ahead of the row sum (in the trial modes the
+      // extra live register costs more than the latency it hides)
+      float bi = 0.f;
+      if (!TRIAL && MODE != FWD_Y && valid && lane == 0) bi = __ldg(b + row);
       if (MF && valid) {
         // matrix-free: the entries of the row from the ray geometry (mf.cuh)
         const int64_t per = (int64_t)A.Pu * A.Pv;
@@ -320,14 +324,15 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
         if (MODE == FWD_Y) {
           r[row] = sx;
         } else {
-          const float ri = __fsub_rn(sx, __ldg(b + row));
+          if (TRIAL) bi = __ldg(b + row);
+          const float ri = __fsub_rn(sx, bi);
           r[row] = ri;
           if (BF && rs) rs[row] = __fmul_rn(sc, ri);
           ff_add_prod(a0, ri, ri);
           if (TRIAL) {
             ff_add_prod(a1, sd, sd);
             if (TWO) {
-              const float ri2 = __fsub_rn(sx2, __ldg(b + row));
+              const float ri2 = __fsub_rn(sx2, bi);
               st->vM[RM_RT2][row] = ri2;
               if (BF) st->vM[RM_RTS2][row] = __fmul_rn(sc, ri2);
               ff_add_prod(c0, ri2, ri2);
@@ -547,6 +552,16 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
     // planes (lane 0: -(w_0 + w_1 + w_2) at j; lanes 1..3: w_e at j - e),
     // loaded ahead of the projection loop
     float c = 0.f;
+    float hh = 0.f;  // lane 0: h_tau(D_j x), for TV_tau(x)
+    if (MODE != BWD_SOLVER && MODE != BWD_ADJ && valid && lane < 4) {
+      // plain modes: the lane's Huber weights from x, evaluated ahead of the
+      // projection loop (lanes 1..3 at the backward neighbours)
+      Huber hw;
+      huber_at(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, hw);
+      c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2])
+                    : (lane == 1 ? hw.w[0] : (lane == 2 ? hw.w[1] : hw.w[2]));
+      hh = hw.h;
+    }
     if (MODE == BWD_SOLVER && valid && lane < 4) {
       const float *__restrict__ W = st->w;
       if (lane == 0)
@@ -599,13 +614,6 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
       if (valid && lane == 0) g[j] = s;
       continue;
     }
-    Huber hw;
-    hw.h = 0.f;
-    if (MODE != BWD_SOLVER && valid && lane < 4) {
-      huber_at(x, ix - (lane == 1), iy - (lane == 2), iz - (lane == 3), n, tau, hw);
-      c = lane == 0 ? -__fadd_rn(__fadd_rn(hw.w[0], hw.w[1]), hw.w[2])
-                    : (lane == 1 ? hw.w[0] : (lane == 2 ? hw.w[1] : hw.w[2]));
-    }
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 2, G));
     c = __fadd_rn(c, __shfl_down_sync(FULL, c, 1, G));
     if (MODE == BWD_VJP) {
@@ -616,7 +624,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
       const float gj = __fmaf_rn(alpha, c, s);
       g[j] = gj;
       if (MODE == BWD_INIT || MODE == BWD_SOLVER) st->pg[j] = make_float2(x[j], gj);
-      if (MODE != BWD_SOLVER) ff_add(a0, hw.h);
+      if (MODE != BWD_SOLVER) ff_add(a0, hh);
       if (MODE == BWD_SOLVER && kind == SOLVER_GPBB) {
         const float sj = __fsub_rn(x[j], xo[j]);
         ff_add_prod(a1, sj, __fsub_rn(gj, go[j]));
