@@ -490,10 +490,10 @@ def run_batch(args):
             s_.solve("upn", b, alpha, tau, eps, x.zero_())
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
-        moved = 0.0
+        moved = 0.0  # algorithmic bytes of the launches that did work (a trial per f-eval)
         for s_, r in zip(systems, rb):
             bb, bf = solver_launch_bytes(s_.m, s_.N, s_.nnz, storage, "upn")
-            moved += r.g_evals * bb + r.trials * bf
+            moved += r.g_evals * bb + r.f_evals * bf
         peak, _ = measured_peak_gbs()
         res[f"batch48_{storage}"] = {
             "solves_per_s": len(systems) / t_batch, "ms": 1e3 * t_batch,
