@@ -518,8 +518,36 @@ void sweep_free(tvr_sweep_mem *m) {
 
 namespace {
 
+// Grids of the two projections, from their own occupancy (the forward
+// gathers two interleaved arrays and holds 16 sums: fewer blocks fit per SM
+// than for the single-solve kernels) and capped by the rows / columns there are.
+struct SweepGrids {
+  int rows_two, rows_one, cols;
+};
+
+SweepGrids sweep_grids(const MatDev &A, int device) {
+  auto cap = [](int g, int64_t items) {
+    const int64_t need = (items + TVR_BLOCK / 4 - 1) / (TVR_BLOCK / 4);  // 4 lanes per row / column
+    return (int)(need < 1 ? 1 : (need < g ? need : g));
+  };
+  const bool bf = A.bf16;
+  SweepGrids g;
+  g.rows_two = cap(occupancy_grid(bf ? (const void *)k_spmm_rows<true, true>
+                                     : (const void *)k_spmm_rows<true, false>,
+                                  TVR_BLOCK, device),
+                   A.m);
+  g.rows_one = cap(occupancy_grid(bf ? (const void *)k_spmm_rows<false, true>
+                                     : (const void *)k_spmm_rows<false, false>,
+                                  TVR_BLOCK, device),
+                   A.m);
+  g.cols = cap(occupancy_grid(bf ? (const void *)k_spmm_cols<true> : (const void *)k_spmm_cols<false>,
+                              TVR_BLOCK, device),
+               A.N);
+  return g;
+}
+
 void sweep_pass(const MatDev &A, const SweepBufs &B, SweepDev *sd, int solver, const Workspace &ws,
-                int gN, int gM, const float *bd, cudaStream_t s) {
+                const SweepGrids &sg, int gN, int gM, const float *bd, cudaStream_t s) {
   const bool bf = A.bf16;
   if (solver == SOLVER_UPN) {
     if (bf)
@@ -528,15 +556,15 @@ void sweep_pass(const MatDev &A, const SweepBufs &B, SweepDev *sd, int solver, c
       k_sw_yform<false><<<gM > gN ? gM : gN, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
   }
   if (bf)
-    k_spmm_cols<true><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
+    k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
   else
-    k_spmm_cols<false><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
+    k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
   k_sw_bwd_post<false><<<gN, TVR_BLOCK, 0, s>>>(A, B.S, sd, ws.bwd);
   k_sw_step<<<gN, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, sd, ws.step);
   if (bf)
-    k_spmm_rows<true, true><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
+    k_spmm_rows<true, true><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
   else
-    k_spmm_rows<true, false><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
+    k_spmm_rows<true, false><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
   if (bf)
     k_sw_fwd_post<false, true><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
   else
@@ -655,16 +683,17 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   TVR_CUDA(cudaMemcpyAsync(C.sd, &h, sizeof(SweepDev), cudaMemcpyHostToDevice, s));
   const MatDev A = sys->mat();
   const Workspace &ws = sys->ws;
+  const SweepGrids sg = sweep_grids(A, sys->device);
   // initial residuals and gradients
   const float *xinit = method == SOLVER_UPN ? B.Y : B.P0;
   if (A.bf16) {
-    k_spmm_rows<false, true><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
+    k_spmm_rows<false, true><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
     k_sw_fwd_post<true, true><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
-    k_spmm_cols<true><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
+    k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
   } else {
-    k_spmm_rows<false, false><<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
+    k_spmm_rows<false, false><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
     k_sw_fwd_post<true, false><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
-    k_spmm_cols<false><<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
+    k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
   }
   k_sw_bwd_post<true><<<gN, TVR_BLOCK, 0, s>>>(A, B.S, C.sd, ws.bwd);
   TVR_CUDA(cudaGetLastError());
@@ -674,7 +703,7 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   int64_t passes = 0;
   bool all_done = false;
   while (!all_done && passes < max_passes) {
-    for (int i = 0; i < o.batch; ++i) sweep_pass(A, B, C.sd, method, ws, gN, gM, bd, s);
+    for (int i = 0; i < o.batch; ++i) sweep_pass(A, B, C.sd, method, ws, sg, gN, gM, bd, s);
     TVR_CUDA(cudaGetLastError());
     passes += o.batch;
     TVR_CUDA(cudaMemcpyAsync(C.flag, C.sd, sizeof(SweepDev), cudaMemcpyDeviceToHost, s));
