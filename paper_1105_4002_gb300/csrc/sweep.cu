@@ -25,7 +25,9 @@
 namespace {
 
 constexpr int KS = 8;               // columns of a sweep
-constexpr int kSweepMaxGrid = 512;  // blocks of a reducing sweep kernel (partials: grid * KS * 4)
+// blocks of a reducing sweep kernel: its partials (grid * KS * 4 values) fill
+// at most a reduction slot
+constexpr int kSweepMaxGrid = TVR_MAX_GRID * TVR_RMAX / (KS * 4);
 
 struct SweepDev {
   DevState col[KS];
@@ -522,7 +524,8 @@ namespace {
 // gathers two interleaved arrays and holds 16 sums: fewer blocks fit per SM
 // than for the single-solve kernels) and capped by the rows / columns there are.
 struct SweepGrids {
-  int rows_two, rows_one, cols;
+  int rows_two, rows_one, cols;             // projections
+  int yform, bwd_post, step, fwd_post;      // one thread per (index, column)
 };
 
 SweepGrids sweep_grids(const MatDev &A, int device) {
@@ -543,32 +546,49 @@ SweepGrids sweep_grids(const MatDev &A, int device) {
   g.cols = cap(occupancy_grid(bf ? (const void *)k_spmm_cols<true> : (const void *)k_spmm_cols<false>,
                               TVR_BLOCK, device),
                A.N);
+  // the (index, column) kernels: one resident wave, at most a reduction slot's worth
+  auto wave = [](int g, int64_t items) {
+    const int64_t need = (items * KS + TVR_BLOCK - 1) / TVR_BLOCK;
+    int64_t b = need < g ? need : g;
+    if (b > kSweepMaxGrid) b = kSweepMaxGrid;
+    return (int)(b < 1 ? 1 : b);
+  };
+  const int64_t mx = A.N > A.m ? A.N : A.m;
+  g.yform = wave(occupancy_grid(bf ? (const void *)k_sw_yform<true> : (const void *)k_sw_yform<false>,
+                                TVR_BLOCK, device),
+                 mx);
+  g.bwd_post = wave(occupancy_grid((const void *)k_sw_bwd_post<false>, TVR_BLOCK, device), A.N);
+  g.step = wave(occupancy_grid((const void *)k_sw_step, TVR_BLOCK, device), A.N);
+  g.fwd_post = wave(occupancy_grid(bf ? (const void *)k_sw_fwd_post<false, true>
+                                      : (const void *)k_sw_fwd_post<false, false>,
+                                   TVR_BLOCK, device),
+                    A.m);
   return g;
 }
 
 void sweep_pass(const MatDev &A, const SweepBufs &B, SweepDev *sd, int solver, const Workspace &ws,
-                const SweepGrids &sg, int gN, int gM, const float *bd, cudaStream_t s) {
+                const SweepGrids &sg, const float *bd, cudaStream_t s) {
   const bool bf = A.bf16;
   if (solver == SOLVER_UPN) {
     if (bf)
-      k_sw_yform<true><<<gM > gN ? gM : gN, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
+      k_sw_yform<true><<<sg.yform, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
     else
-      k_sw_yform<false><<<gM > gN ? gM : gN, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
+      k_sw_yform<false><<<sg.yform, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
   }
   if (bf)
     k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
   else
     k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
-  k_sw_bwd_post<false><<<gN, TVR_BLOCK, 0, s>>>(A, B.S, sd, ws.bwd);
-  k_sw_step<<<gN, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, sd, ws.step);
+  k_sw_bwd_post<false><<<sg.bwd_post, TVR_BLOCK, 0, s>>>(A, B.S, sd, ws.bwd);
+  k_sw_step<<<sg.step, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, sd, ws.step);
   if (bf)
     k_spmm_rows<true, true><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
   else
     k_spmm_rows<true, false><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
   if (bf)
-    k_sw_fwd_post<false, true><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
+    k_sw_fwd_post<false, true><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
   else
-    k_sw_fwd_post<false, false><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
+    k_sw_fwd_post<false, false><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
 }
 
 }  // namespace
@@ -639,7 +659,6 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
     TVR_CUDA(cudaMemcpyAsync(sys->stage_sweepX, X, sizeof(float) * k * N, cudaMemcpyHostToDevice, s));
     x0 = sys->stage_sweepX;
   }
-  const int gN = sweep_grid(N, kSweepMaxGrid), gM = sweep_grid(m, kSweepMaxGrid);
   k_interleave<<<sweep_grid(N, 4096), TVR_BLOCK, 0, s>>>(x0, k, N, B.P0, B.Y);
   TVR_CUDA(cudaMemsetAsync(B.U, 0, sizeof(float) * KS * m, s));
   // per-column states
@@ -688,14 +707,14 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   const float *xinit = method == SOLVER_UPN ? B.Y : B.P0;
   if (A.bf16) {
     k_spmm_rows<false, true><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
-    k_sw_fwd_post<true, true><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
+    k_sw_fwd_post<true, true><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
     k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
   } else {
     k_spmm_rows<false, false><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
-    k_sw_fwd_post<true, false><<<gM, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
+    k_sw_fwd_post<true, false><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
     k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
   }
-  k_sw_bwd_post<true><<<gN, TVR_BLOCK, 0, s>>>(A, B.S, C.sd, ws.bwd);
+  k_sw_bwd_post<true><<<sg.bwd_post, TVR_BLOCK, 0, s>>>(A, B.S, C.sd, ws.bwd);
   TVR_CUDA(cudaGetLastError());
   // passes in batches; the host reads the column states once per batch
   const int64_t trials = (o.bt_max > o.gpbb_max_trials ? o.bt_max : o.gpbb_max_trials) + 2;
@@ -703,7 +722,7 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   int64_t passes = 0;
   bool all_done = false;
   while (!all_done && passes < max_passes) {
-    for (int i = 0; i < o.batch; ++i) sweep_pass(A, B, C.sd, method, ws, sg, gN, gM, bd, s);
+    for (int i = 0; i < o.batch; ++i) sweep_pass(A, B, C.sd, method, ws, sg, bd, s);
     TVR_CUDA(cudaGetLastError());
     passes += o.batch;
     TVR_CUDA(cudaMemcpyAsync(C.flag, C.sd, sizeof(SweepDev), cudaMemcpyDeviceToHost, s));
