@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
 
 // ---- gradient after the back projection: g = S + alpha grad TV_tau at the base point ----
 template <bool INIT>
-__global__ void __launch_bounds__(TVR_BLOCK)
+__global__ void __launch_bounds__(TVR_BLOCK, 4)
     k_sw_bwd_post(MatDev A, const float *__restrict__ S, SweepDev *sd, RedSlot slot) {
   ColIter it;
   DevState *st = &sd->col[it.c];
