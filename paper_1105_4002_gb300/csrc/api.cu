@@ -174,7 +174,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
     slots[k]->counter = (unsigned *)(b + part);
     slots[k]->out = (double *)(b + part + 256);
   }
-  kernel_grids(sys->ws, sys->device, sys->m, sys->N);
+  kernel_grids(sys->ws, sys->mat(), sys->device);
   BUILD_CUDA(cudaMalloc(&sys->phi_ws, sizeof(double) * 4));
   BUILD_CUDA(cudaStreamSynchronize(s));
   BUILD_CUDA(cudaGetLastError());

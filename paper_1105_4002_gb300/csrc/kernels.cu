@@ -151,7 +151,8 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool BF, bool MF = false>
 __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
-                                            : (MODE == FWD_TRIAL_X || MODE == FWD_TRIAL_2
+                                            : (MODE == FWD_TRIAL || MODE == FWD_TRIAL_X ||
+                                                       MODE == FWD_TRIAL_2
                                                    ? TVR_TRIAL_MIN_BLOCKS
                                                    : TVR_FWD_MIN_BLOCKS))
     k_forward(MatDev A, const float *__restrict__ xin, const float *__restrict__ b,
@@ -731,34 +732,6 @@ int occupancy_grid(const void *kernel, int block, int device) {
   return g < TVR_MAX_GRID ? g : TVR_MAX_GRID;
 }
 
-void kernel_grids(Workspace &ws, int device, int64_t m, int64_t N) {
-  // at most one wave of resident blocks, and no more blocks than the work
-  // needs (rows or columns in groups of TVR_BLOCK / lanes, voxels in groups of
-  // TVR_BLOCK), so that the kernels of small systems leave room for others
-  // running concurrently on other streams
-  auto cap = [](int grid, int64_t need) {
-    need = need < 1 ? 1 : need;
-    return (int)(need < grid ? need : grid);
-  };
-  const int64_t rows = (m + TVR_BLOCK / kRowLanes - 1) / (TVR_BLOCK / kRowLanes);
-  const int64_t cols = (N + TVR_BLOCK / kColLanes - 1) / (TVR_BLOCK / kColLanes);
-  const int64_t vox = (N + TVR_BLOCK - 1) / TVR_BLOCK;
-  const int64_t fwd_need = rows > vox ? rows : vox;
-  ws.grid_fwd = cap(
-      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL, false>, TVR_BLOCK, device),
-      fwd_need);
-  ws.grid_trial_x = cap(
-      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_X, false>, TVR_BLOCK, device),
-      fwd_need);
-  ws.grid_trial_2 = cap(
-      occupancy_grid((const void *)k_forward<kRowLanes, FWD_TRIAL_2, false>, TVR_BLOCK, device),
-      fwd_need);
-  ws.grid_bwd = cap(
-      occupancy_grid((const void *)k_backward<kColLanes, BWD_SOLVER, false>, TVR_BLOCK, device),
-      cols);
-  ws.grid_elem = cap(occupancy_grid((const void *)k_tv_value, TVR_BLOCK, device), vox);
-}
-
 // Launch with programmatic stream serialization (the kernel calls pdl_enter
 // first), so that its blocks are scheduled while the predecessor drains.
 template <typename... P, typename... A>
@@ -786,6 +759,30 @@ template <int MODE>
 auto bwd_kernel(const MatDev &A) {
   return A.mf ? k_backward<kColLanes, MODE, false, true>
               : (A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>);
+}
+
+// Grids of the hot kernels, each from the occupancy of the instance that runs
+// for this system's storage (FP32, BF16 or matrix-free values differ in
+// registers): at most one wave of resident blocks, and no more blocks than the
+// work needs (rows or columns in groups of TVR_BLOCK / lanes, voxels in groups
+// of TVR_BLOCK), so that the kernels of small systems leave room for others
+// running concurrently on other streams.
+void kernel_grids(Workspace &ws, const MatDev &A, int device) {
+  auto cap = [](int grid, int64_t need) {
+    need = need < 1 ? 1 : need;
+    return (int)(need < grid ? need : grid);
+  };
+  auto occ = [&](const void *k) { return occupancy_grid(k, TVR_BLOCK, device); };
+  const int64_t rows = (A.m + TVR_BLOCK / kRowLanes - 1) / (TVR_BLOCK / kRowLanes);
+  const int64_t cols = (A.N + TVR_BLOCK / kColLanes - 1) / (TVR_BLOCK / kColLanes);
+  const int64_t vox = (A.N + TVR_BLOCK - 1) / TVR_BLOCK;
+  const int64_t fwd_need = rows > vox ? rows : vox;
+  ws.grid_fwd = cap(occ((const void *)fwd_kernel<FWD_RESID>(A)), rows);
+  ws.grid_trial = cap(occ((const void *)fwd_kernel<FWD_TRIAL>(A)), fwd_need);
+  ws.grid_trial_x = cap(occ((const void *)fwd_kernel<FWD_TRIAL_X>(A)), fwd_need);
+  ws.grid_trial_2 = cap(occ((const void *)fwd_kernel<FWD_TRIAL_2>(A)), fwd_need);
+  ws.grid_bwd = cap(occ((const void *)bwd_kernel<BWD_SOLVER>(A)), cols);
+  ws.grid_elem = cap(occ((const void *)k_tv_value), vox);
 }
 
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
@@ -863,7 +860,7 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
                                       : fwd_kernel<FWD_TRIAL>(A);
   const int grid = solver == SOLVER_UPN   ? ws.grid_trial_x
                    : solver == PASS_GPBB2 ? ws.grid_trial_2
-                                          : ws.grid_fwd;
+                                          : ws.grid_trial;
   launch_pdl(trial, grid, s, A, nullptr, nullptr, nullptr, ws.fwd, st, slot(0), nullptr);
   mark(0, 1);
 }

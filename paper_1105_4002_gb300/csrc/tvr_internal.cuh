@@ -441,7 +441,7 @@ __device__ __forceinline__ void voxel_of(const MatDev &A, int64_t j, int &ix, in
 
 struct Workspace {
   RedSlot fwd, bwd, step, yf, tv, gmap;
-  int grid_fwd, grid_bwd, grid_elem, grid_trial_x, grid_trial_2;
+  int grid_fwd, grid_bwd, grid_elem, grid_trial, grid_trial_x, grid_trial_2;
 };
 
 // Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from
@@ -537,4 +537,4 @@ cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream
 void free_matrix(MatStore &A);
 
 int occupancy_grid(const void *kernel, int block, int device);
-void kernel_grids(Workspace &ws, int device, int64_t m, int64_t N);
+void kernel_grids(Workspace &ws, const MatDev &A, int device);
