@@ -528,6 +528,7 @@ def run_batch(args):
         res[f"sweep8_128cubed_{storage}"] = {
             "solves_per_s": 8 / t_sw, "ms": 1e3 * t_sw, "single_solves_per_s": 8 / t_single,
             "converged": sum(r.status == 0 for r in rs), "iters": [r.iters for r in rs],
+            "lanes_rows_cols": list(rs[0].lanes),
             "single_iters": its}
         del sysm, X
         torch.cuda.empty_cache()

@@ -232,6 +232,12 @@ typedef struct tvr_solve_opts {
                                after a rejection (step beta^2 theta) and uses it when the first
                                is rejected: the same decisions and iterates as one point per
                                pass, in fewer passes over A */
+  int32_t sweep_lanes;      /* tvr_solve_sweep: lanes per row / column of its two projections
+                               (the row split): 0 (default) = chosen by timing 2, 4 and 8 lanes
+                               on the system at its first sweep, kept for later sweeps on
+                               systems of the same shape on the same GPU; 2, 4 or 8 = fixed.
+                               Changes only the order of additions */
+  int32_t reserved;
   double gpbb_sigma;        /* default 0.1 (Sec. III-A) */
   double gpbb_beta0;        /* default 0.95 (Alg. 1) */
   double rho_L;             /* BT factor (Alg. 2), default 2 */
@@ -249,7 +255,9 @@ typedef struct tvr_solve_info {
   int32_t trials;       /* rejected line-search / BT trials in total */
   int32_t passes;       /* passes launched, including no-op passes after the stop */
   int32_t history_used; /* records written to opts->history */
-  int32_t reserved;
+  int32_t lanes;        /* tvr_solve_sweep: the row split its projections ran with, lanes per
+                           row (forward) | lanes per column (back projection) << 8; 0 for the
+                           other solvers */
   double phi;           /* phi(x*) evaluated afresh at the returned point */
   double gnorm;         /* ||G|| of the last iteration */
   double gnorm0;        /* ||G|| of iteration 0 */

@@ -71,6 +71,7 @@ class SolveOptions:
     use_graph: bool = True
     batch: int = 32
     gpbb_points: int = 2  # GPBB trial points per forward pass (1 or 2; same iterates)
+    sweep_lanes: int = 0  # solve_sweep row split: 0 = autotuned, or 2, 4, 8 lanes per row
     gpbb_sigma: float = 0.1
     gpbb_beta0: float = 0.95
     rho_L: float = 2.0
@@ -95,6 +96,7 @@ class SolveResult:
     theta: float
     mu: float
     history: np.ndarray | None = None
+    lanes: tuple[int, int] = (0, 0)  # solve_sweep: lanes per (row, column) of its projections
 
     @property
     def ok(self) -> bool:
@@ -214,7 +216,8 @@ class System:
         co = _capi.SolveOpts()
         lib().tvr_solve_opts_default(ctypes.byref(co))
         for f in ("k_max", "stop_mode", "gpbb_K", "gpbb_max_trials", "bt_max", "batch",
-                  "gpbb_points", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
+                  "gpbb_points", "sweep_lanes", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar",
+                  "mu_bar"):
             setattr(co, f, getattr(o, f))
         co.use_graph = 1 if o.use_graph else 0
         hist = None
@@ -252,14 +255,16 @@ class System:
         return [SolveResult(status=i.status, iters=i.iters, f_evals=i.f_evals, g_evals=i.g_evals,
                             trials=i.trials, passes=i.passes, phi=i.phi, gnorm=i.gnorm,
                             gnorm0=i.gnorm0, stop_value=i.stop_value, L=i.L, theta=i.theta,
-                            mu=i.mu) for i in infos]
+                            mu=i.mu, lanes=(i.lanes & 0xff, (i.lanes >> 8) & 0xff))
+                for i in infos]
 
     def _opts(self, opts):
         o = opts or SolveOptions()
         co = _capi.SolveOpts()
         lib().tvr_solve_opts_default(ctypes.byref(co))
         for f in ("k_max", "stop_mode", "gpbb_K", "gpbb_max_trials", "bt_max", "batch",
-                  "gpbb_points", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar", "mu_bar"):
+                  "gpbb_points", "sweep_lanes", "gpbb_sigma", "gpbb_beta0", "rho_L", "L_bar",
+                  "mu_bar"):
             setattr(co, f, getattr(o, f))
         co.use_graph = 1 if o.use_graph else 0
         return co

@@ -37,7 +37,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("stop_mode", ctypes.c_int32), ("gpbb_K", ctypes.c_int32),
                 ("gpbb_max_trials", ctypes.c_int32), ("bt_max", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("gpbb_points", ctypes.c_int32),
+                ("gpbb_points", ctypes.c_int32), ("sweep_lanes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
                 ("gpbb_sigma", ctypes.c_double), ("gpbb_beta0", ctypes.c_double),
                 ("rho_L", ctypes.c_double), ("L_bar", ctypes.c_double), ("mu_bar", ctypes.c_double),
                 ("history", ctypes.c_void_p), ("history_len", ctypes.c_int64)]
@@ -46,7 +47,7 @@ class SolveOpts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("f_evals", ctypes.c_int32),
                 ("g_evals", ctypes.c_int32), ("trials", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("history_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("history_used", ctypes.c_int32), ("lanes", ctypes.c_int32),
                 ("phi", ctypes.c_double), ("gnorm", ctypes.c_double), ("gnorm0", ctypes.c_double),
                 ("stop_value", ctypes.c_double), ("L", ctypes.c_double), ("theta", ctypes.c_double),
                 ("mu", ctypes.c_double)]

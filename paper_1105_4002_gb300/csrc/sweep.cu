@@ -17,6 +17,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "ctrl.cuh"
@@ -127,16 +130,20 @@ __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
 
 // ---- projections shared by all columns ----
-template <bool TWO, bool BF>
+// G lanes per row (the row split): each lane reads 4 entries with one 16-byte
+// load of indices and one of values, at stride 4 G; any G covers every entry
+// of the lane-interleaved storage exactly once, only the order of additions
+// changes.
+template <int G, bool TWO, bool BF>
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_spmm_rows(MatDev A, const float *__restrict__ in0, const float *__restrict__ in1,
                 float *__restrict__ out0, float *__restrict__ out1, const SweepDev *sd, int init) {
+  static_assert(G == 2 || G == 4 || G == 8, "lanes per row");
   if (!init) {
     bool any = false;
     for (int c = 0; c < KS; ++c) any = any || !sd->col[c].done;
     if (!any) return;
   }
-  constexpr int G = 4;
   const int lane = threadIdx.x & (G - 1), sub = (threadIdx.x & 31) / G;
   const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
   const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
@@ -199,16 +206,16 @@ __global__ void __launch_bounds__(TVR_BLOCK)
   }
 }
 
-template <bool BF>
+template <int G, bool BF>
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_spmm_cols(MatDev A, const float *__restrict__ in, float *__restrict__ out, const SweepDev *sd,
                 int init) {
+  static_assert(G == 2 || G == 4 || G == 8, "lanes per column");
   if (!init) {
     bool any = false;
     for (int c = 0; c < KS; ++c) any = any || (!sd->col[c].done && sd->col[c].need_grad);
     if (!any) return;
   }
-  constexpr int G = 4;
   const int lane = threadIdx.x & (G - 1), sub = (threadIdx.x & 31) / G;
   const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
   const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
@@ -520,36 +527,57 @@ void sweep_free(tvr_sweep_mem *m) {
 
 namespace {
 
-// Grids of the two projections, from their own occupancy (the forward
-// gathers two interleaved arrays and holds 16 sums: fewer blocks fit per SM
-// than for the single-solve kernels) and capped by the rows / columns there are.
+using RowsFn = void (*)(MatDev, const float *, const float *, float *, float *, const SweepDev *,
+                       int);
+using ColsFn = void (*)(MatDev, const float *, float *, const SweepDev *, int);
+
+template <bool TWO>
+RowsFn rows_fn(int G, bool bf) {
+  if (bf) return G == 2 ? k_spmm_rows<2, TWO, true> : G == 8 ? k_spmm_rows<8, TWO, true>
+                                                              : k_spmm_rows<4, TWO, true>;
+  return G == 2 ? k_spmm_rows<2, TWO, false> : G == 8 ? k_spmm_rows<8, TWO, false>
+                                                     : k_spmm_rows<4, TWO, false>;
+}
+ColsFn cols_fn(int G, bool bf) {
+  if (bf) return G == 2 ? k_spmm_cols<2, true> : G == 8 ? k_spmm_cols<8, true> : k_spmm_cols<4, true>;
+  return G == 2 ? k_spmm_cols<2, false> : G == 8 ? k_spmm_cols<8, false> : k_spmm_cols<4, false>;
+}
+
+// Launch configuration of a sweep: the row split of each projection (lanes
+// per row / column) with its kernel and grid -- the grid from the kernel's own
+// occupancy (the forward gathers two interleaved arrays and holds 16 sums:
+// fewer blocks fit per SM than for the single-solve kernels), capped by the
+// rows / columns there are -- and one resident wave for each (index, column)
+// kernel, at most a reduction slot's worth.
 struct SweepGrids {
-  int rows_two, rows_one, cols;             // projections
-  int yform, bwd_post, step, fwd_post;      // one thread per (index, column)
+  int lanes_rows = 4, lanes_cols = 4;
+  RowsFn rows_two = nullptr, rows_one = nullptr;
+  ColsFn cols = nullptr;
+  int g_rows_two = 1, g_rows_one = 1, g_cols = 1;  // projections
+  int yform = 1, bwd_post = 1, step = 1, fwd_post = 1;
 };
 
-SweepGrids sweep_grids(const MatDev &A, int device) {
-  auto cap = [](int g, int64_t items) {
-    const int64_t need = (items + TVR_BLOCK / 4 - 1) / (TVR_BLOCK / 4);  // 4 lanes per row / column
-    return (int)(need < 1 ? 1 : (need < g ? need : g));
-  };
+int proj_grid(const void *k, int lanes, int64_t items, int device) {
+  const int g = occupancy_grid(k, TVR_BLOCK, device);
+  const int64_t per = TVR_BLOCK / lanes;  // rows or columns per block
+  const int64_t need = (items + per - 1) / per;
+  return (int)(need < 1 ? 1 : (need < g ? need : g));
+}
+
+SweepGrids sweep_grids(const MatDev &A, int device, int lanes_rows, int lanes_cols) {
   const bool bf = A.bf16;
   SweepGrids g;
-  g.rows_two = cap(occupancy_grid(bf ? (const void *)k_spmm_rows<true, true>
-                                     : (const void *)k_spmm_rows<true, false>,
-                                  TVR_BLOCK, device),
-                   A.m);
-  g.rows_one = cap(occupancy_grid(bf ? (const void *)k_spmm_rows<false, true>
-                                     : (const void *)k_spmm_rows<false, false>,
-                                  TVR_BLOCK, device),
-                   A.m);
-  g.cols = cap(occupancy_grid(bf ? (const void *)k_spmm_cols<true> : (const void *)k_spmm_cols<false>,
-                              TVR_BLOCK, device),
-               A.N);
-  // the (index, column) kernels: one resident wave, at most a reduction slot's worth
-  auto wave = [](int g, int64_t items) {
+  g.lanes_rows = lanes_rows;
+  g.lanes_cols = lanes_cols;
+  g.rows_two = rows_fn<true>(lanes_rows, bf);
+  g.rows_one = rows_fn<false>(lanes_rows, bf);
+  g.cols = cols_fn(lanes_cols, bf);
+  g.g_rows_two = proj_grid((const void *)g.rows_two, lanes_rows, A.m, device);
+  g.g_rows_one = proj_grid((const void *)g.rows_one, lanes_rows, A.m, device);
+  g.g_cols = proj_grid((const void *)g.cols, lanes_cols, A.N, device);
+  auto wave = [](int gr, int64_t items) {
     const int64_t need = (items * KS + TVR_BLOCK - 1) / TVR_BLOCK;
-    int64_t b = need < g ? need : g;
+    int64_t b = need < gr ? need : gr;
     if (b > kSweepMaxGrid) b = kSweepMaxGrid;
     return (int)(b < 1 ? 1 : b);
   };
@@ -566,6 +594,79 @@ SweepGrids sweep_grids(const MatDev &A, int device) {
   return g;
 }
 
+// Row-split autotuner: times each projection with 2, 4 and 8 lanes per row /
+// column on this system (one untimed and two timed launches each, on buffers
+// cleared for it; the sweep's initialisation overwrites what they write) and
+// keeps the fastest.  The choice is cached per (rows, columns, entries,
+// storage, GPU) for the life of the process.
+struct TuneKey {
+  int64_t m, N, nnz;
+  int bf, device;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(m, N, nnz, bf, device) < std::tie(o.m, o.N, o.nnz, o.bf, o.device);
+  }
+};
+
+int sweep_tune(const MatDev &A, int device, const SweepBufs &B, const SweepDev *sd,
+               cudaStream_t s, int *lanes_rows, int *lanes_cols) {
+  static std::mutex mu;
+  static std::map<TuneKey, std::pair<int, int>> cache;
+  const TuneKey key{A.m, A.N, A.nnz, A.bf16 ? 1 : 0, device};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *lanes_rows = it->second.first;
+      *lanes_cols = it->second.second;
+      return TVR_OK;
+    }
+  }
+  TVR_CUDA(cudaMemsetAsync(B.XB, 0, sizeof(float) * KS * A.N, s));
+  TVR_CUDA(cudaMemsetAsync(B.DD, 0, sizeof(float) * KS * A.N, s));
+  TVR_CUDA(cudaMemsetAsync(B.RG, 0, sizeof(float) * KS * A.m, s));
+  cudaEvent_t e0, e1;
+  TVR_CUDA(cudaEventCreate(&e0));
+  TVR_CUDA(cudaEventCreate(&e1));
+  auto timed = [&](auto launch, float *ms) -> int {
+    launch();
+    TVR_CUDA(cudaEventRecord(e0, s));
+    launch();
+    launch();
+    TVR_CUDA(cudaEventRecord(e1, s));
+    TVR_CUDA(cudaEventSynchronize(e1));
+    TVR_CUDA(cudaGetLastError());
+    TVR_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return TVR_OK;
+  };
+  const int cand[3] = {2, 4, 8};
+  float best_r = 0.f, best_c = 0.f;
+  int lr = 4, lc = 4;
+  int rc = TVR_OK;
+  for (int i = 0; i < 3 && rc == TVR_OK; ++i) {
+    const int L = cand[i];
+    const RowsFn fr = rows_fn<true>(L, A.bf16);
+    const int gr = proj_grid((const void *)fr, L, A.m, device);
+    float tr = 0.f;
+    rc = timed([&] { fr<<<gr, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 1); }, &tr);
+    if (rc != TVR_OK) break;
+    const ColsFn fc = cols_fn(L, A.bf16);
+    const int gc = proj_grid((const void *)fc, L, A.N, device);
+    float tc = 0.f;
+    rc = timed([&] { fc<<<gc, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 1); }, &tc);
+    if (rc != TVR_OK) break;
+    if (i == 0 || tr < best_r) { best_r = tr; lr = L; }
+    if (i == 0 || tc < best_c) { best_c = tc; lc = L; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TVR_OK) return rc;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = {lr, lc};
+  *lanes_rows = lr;
+  *lanes_cols = lc;
+  return TVR_OK;
+}
+
 void sweep_pass(const MatDev &A, const SweepBufs &B, SweepDev *sd, int solver, const Workspace &ws,
                 const SweepGrids &sg, const float *bd, cudaStream_t s) {
   const bool bf = A.bf16;
@@ -575,16 +676,10 @@ void sweep_pass(const MatDev &A, const SweepBufs &B, SweepDev *sd, int solver, c
     else
       k_sw_yform<false><<<sg.yform, TVR_BLOCK, 0, s>>>(A, B.RG, sd, ws.yf);
   }
-  if (bf)
-    k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
-  else
-    k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
+  sg.cols<<<sg.g_cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 0);
   k_sw_bwd_post<false><<<sg.bwd_post, TVR_BLOCK, 0, s>>>(A, B.S, sd, ws.bwd);
   k_sw_step<<<sg.step, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, sd, ws.step);
-  if (bf)
-    k_spmm_rows<true, true><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
-  else
-    k_spmm_rows<true, false><<<sg.rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
+  sg.rows_two<<<sg.g_rows_two, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 0);
   if (bf)
     k_sw_fwd_post<false, true><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, B.ZD, B.RG, sd, ws.fwd);
   else
@@ -615,7 +710,8 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   if (o.k_max < 1 || o.gpbb_K < 0 || o.gpbb_K > 8 || o.gpbb_max_trials < 0 || o.bt_max < 0 ||
       o.batch < 1 || o.batch > 1024 || !(o.rho_L > 1.0) || !(o.L_bar > 0.0) || !(o.mu_bar >= 0.0) ||
       !(o.gpbb_sigma > 0.0 && o.gpbb_sigma < 1.0) || !(o.gpbb_beta0 > 0.0 && o.gpbb_beta0 < 1.0) ||
-      (o.stop_mode != TVR_STOP_REL && o.stop_mode != TVR_STOP_PER_N))
+      (o.stop_mode != TVR_STOP_REL && o.stop_mode != TVR_STOP_PER_N) ||
+      (o.sweep_lanes != 0 && o.sweep_lanes != 2 && o.sweep_lanes != 4 && o.sweep_lanes != 8))
     return fail(TVR_ERR_ARG, "tvr_solve_sweep: invalid options");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = sys->N, m = sys->m;
@@ -702,18 +798,20 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
   TVR_CUDA(cudaMemcpyAsync(C.sd, &h, sizeof(SweepDev), cudaMemcpyHostToDevice, s));
   const MatDev A = sys->mat();
   const Workspace &ws = sys->ws;
-  const SweepGrids sg = sweep_grids(A, sys->device);
+  // row split of the projections: given, or timed on this system (before the
+  // initialisation, which overwrites the buffers the timing writes)
+  int lanes_rows = o.sweep_lanes, lanes_cols = o.sweep_lanes;
+  if (o.sweep_lanes == 0)
+    if (int rc = sweep_tune(A, sys->device, B, C.sd, s, &lanes_rows, &lanes_cols)) return rc;
+  const SweepGrids sg = sweep_grids(A, sys->device, lanes_rows, lanes_cols);
   // initial residuals and gradients
   const float *xinit = method == SOLVER_UPN ? B.Y : B.P0;
-  if (A.bf16) {
-    k_spmm_rows<false, true><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
+  sg.rows_one<<<sg.g_rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
+  if (A.bf16)
     k_sw_fwd_post<true, true><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
-    k_spmm_cols<true><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
-  } else {
-    k_spmm_rows<false, false><<<sg.rows_one, TVR_BLOCK, 0, s>>>(A, xinit, nullptr, B.Z, nullptr, C.sd, 1);
+  else
     k_sw_fwd_post<true, false><<<sg.fwd_post, TVR_BLOCK, 0, s>>>(A, bd, B.Z, nullptr, B.RG, C.sd, ws.fwd);
-    k_spmm_cols<false><<<sg.cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
-  }
+  sg.cols<<<sg.g_cols, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, C.sd, 1);
   k_sw_bwd_post<true><<<sg.bwd_post, TVR_BLOCK, 0, s>>>(A, B.S, C.sd, ws.bwd);
   TVR_CUDA(cudaGetLastError());
   // passes in batches; the host reads the column states once per batch
@@ -753,6 +851,7 @@ extern "C" int tvr_solve_sweep(const tvr_system *csys, int32_t method, const flo
       in.g_evals = d.g_evals;
       in.trials = d.total_trials;
       in.passes = (int32_t)passes;
+      in.lanes = lanes_rows | (lanes_cols << 8);
       in.phi = NAN;
       in.gnorm = d.gnorm;
       in.gnorm0 = d.gnorm0;

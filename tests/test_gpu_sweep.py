@@ -26,10 +26,13 @@ def c32():
 
 @pytest.mark.parametrize("method", ["upn", "gp", "gpbb"])
 def test_sweep_columns_equal_single_solves(c32, method):
+    """With the single solves' row split (4 lanes) a column runs exactly their
+    arithmetic."""
     torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions
     X = torch.zeros(len(ALPHAS) * prob.N, device="cuda")
     b = dev_f32(torch, prob.b)
-    res = s.solve_sweep(method, b, ALPHAS, prob.tau, cfg.eps, X)
+    res = s.solve_sweep(method, b, ALPHAS, prob.tau, cfg.eps, X, SolveOptions(sweep_lanes=4))
     Xh = X.cpu().numpy().reshape(len(ALPHAS), prob.N)
     for c, a in enumerate(ALPHAS):
         x1 = torch.zeros(prob.N, device="cuda")
@@ -86,3 +89,54 @@ def test_sweep_bf16(c32):
         x1 = torch.zeros(prob.N, device="cuda")
         s16.solve("upn", b, a, prob.tau, cfg.eps, x1)
         assert res[c].ok and rel_l2(Xh[c], x1.cpu().numpy()) <= 1e-5
+
+
+def _single_spread(torch, s, prob, a, eps, draws=4):
+    """The single solve's x* and how far it moves when b is perturbed at the
+    relative size of float32 rounding (1e-6): a change in the order of the
+    additions moves the stopping iterate about as much."""
+    b = dev_f32(torch, prob.b)
+    x1 = torch.zeros(prob.N, device="cuda")
+    s.solve("upn", b, a, prob.tau, eps, x1)
+    ref = x1.cpu().numpy()
+    rng = np.random.default_rng(0)
+    spread = 0.0
+    for _ in range(draws):
+        pb = dev_f32(torch, prob.b * (1 + 1e-6 * rng.standard_normal(prob.b.size)))
+        s.solve("upn", pb, a, prob.tau, eps, x1.zero_())
+        spread = max(spread, rel_l2(x1.cpu().numpy(), ref))
+    return ref, spread
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_every_row_split_reproduces_the_single_solves(c32, lanes):
+    """The row split (lanes per row / column of the sweep's projections)
+    changes only the order of additions: each column stays within the single
+    solve's own spread under float32-sized perturbations (4 lanes: the same
+    arithmetic)."""
+    torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions
+    X = torch.zeros(len(ALPHAS) * prob.N, device="cuda")
+    b = dev_f32(torch, prob.b)
+    res = s.solve_sweep("upn", b, ALPHAS, prob.tau, cfg.eps, X, SolveOptions(sweep_lanes=lanes))
+    assert all(r.status == 0 and r.lanes == (lanes, lanes) for r in res)
+    Xh = X.cpu().numpy().reshape(len(ALPHAS), prob.N)
+    for c, a in enumerate(ALPHAS):
+        ref, spread = _single_spread(torch, s, prob, a, cfg.eps)
+        d = rel_l2(Xh[c], ref)
+        assert d <= (1e-5 if lanes == 4 else max(1e-5, 3 * spread)), (lanes, a, d, spread)
+
+
+def test_autotuned_row_split_is_a_candidate_and_kept(c32):
+    torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions, System, TVRError
+    b = dev_f32(torch, prob.b)
+    X = torch.zeros(2 * prob.N, device="cuda")
+    r1 = s.solve_sweep("upn", b, ALPHAS[:2], prob.tau, cfg.eps, X)
+    assert r1[0].lanes[0] in (2, 4, 8) and r1[0].lanes[1] in (2, 4, 8)
+    # a second system of the same shape on the same GPU reuses the choice
+    s2 = System(cfg.geometry())
+    r2 = s2.solve_sweep("upn", b, ALPHAS[:2], prob.tau, cfg.eps, X.zero_())
+    assert r2[0].lanes == r1[0].lanes
+    with pytest.raises(TVRError):
+        s.solve_sweep("upn", b, ALPHAS[:2], prob.tau, cfg.eps, X, SolveOptions(sweep_lanes=3))
