@@ -61,8 +61,10 @@ def parse():
     ap.add_argument("--phi-loop", type=int, default=200)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
                     help="values of A: float32, or bfloat16 codes with per-row float32 scale")
-    ap.add_argument("--pattern", default="solve", choices=["solve", "autograd", "batch", "paper"],
-                    help="autograd: phi forward + backward through torch.autograd at 128^3")
+    ap.add_argument("--pattern", default="solve",
+                    choices=["solve", "autograd", "batch", "paper", "grid"],
+                    help="autograd: phi forward + backward through torch.autograd at 128^3; "
+                         "grid: GP, GPBB and UPN over alpha x tau x eps at 64^3")
     return ap.parse_args()
 
 
@@ -544,6 +546,61 @@ def run_batch(args):
         "results": res}), flush=True)
 
 
+def run_grid(args):
+    """The 64^3 problem solved by GP, GPBB and UPN for every alpha in {1e-3,
+    1e-2, 1e-1}, tau in {1e-2, 1e-4} and eps in {1e-4, 1e-6} (relative
+    gradient-map stop), from x0 = 0 on the same data.  Reported per case:
+    status, iterations, gradient and objective evaluations, time to eps and
+    gradient evaluations per second."""
+    import math
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    cfg = synth.get_config(args.config)
+    dev = torch.device("cuda", 0)
+    geom, x_true, z = make_problem(cfg, 0)
+    sysm = tvr.System(geom, storage=args.storage)
+    xt = torch.tensor(x_true, dtype=torch.float32, device=dev)
+    ax = torch.empty(sysm.m, device=dev)
+    sysm.forward(xt, ax)
+    axh = ax.cpu().numpy().astype(np.float64)
+    b = torch.tensor((axh + cfg.noise * np.linalg.norm(axh) / math.sqrt(sysm.m) * z)
+                     .astype(np.float32), device=dev)
+    x = torch.zeros(sysm.N, device=dev)
+    sysm.solve("upn", b, cfg.alpha, cfg.tau, 1e-4, x)          # warm-up (graphs, buffers)
+    cases = []
+    total_evals, total_ms = 0, 0.0
+    for method in ("gp", "gpbb", "upn"):
+        for alpha in (1e-3, 1e-2, 1e-1):
+            for tau in (1e-2, 1e-4):
+                for eps in (1e-4, 1e-6):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    r = sysm.solve(method, b, alpha, tau, eps, x)
+                    torch.cuda.synchronize()
+                    ms = 1e3 * (time.perf_counter() - t0)
+                    cases.append({"method": method, "alpha": alpha, "tau": tau, "eps": eps,
+                                  "status": r.status, "iters": r.iters, "g_evals": r.g_evals,
+                                  "f_evals": r.f_evals, "ms": ms,
+                                  "grad_evals_per_s": r.g_evals / (ms / 1e3)})
+                    total_evals += r.g_evals
+                    total_ms += ms
+    print(json.dumps({
+        "metric": "gradient evaluations/s and time to eps over the GP/GPBB/UPN x alpha x tau x eps "
+                  "grid at 64^3", "value": total_evals / (total_ms / 1e3),
+        "unit": "grad-phi evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "fp32" else "bf16 values, f32 arithmetic",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": cfg.n, "views": cfg.views, "det": cfg.det,
+                   "storage": args.storage, "k_max": 20000},
+        "converged": sum(c["status"] == 0 for c in cases), "cases": cases}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -569,6 +626,10 @@ def main():
     if args.pattern == "paper":
         if rank == 0:
             run_paper(args)
+        return
+    if args.pattern == "grid":
+        if rank == 0:
+            run_grid(args)
         return
 
     import numpy as np

@@ -229,3 +229,27 @@ def test_gpbb_two_points_per_pass_give_the_same_iterates(c32):
     assert np.array_equal(x1, x2)
     assert np.array_equal(r1.history, r2.history)
     assert r1.trials > 0 and r2.passes < r1.passes
+
+
+# the corners of the parameter grid the 64^3 configuration runs (alpha in
+# {1e-3, 1e-2, 1e-1}, tau in {1e-2, 1e-4}) beyond the default (1e-2, 1e-4)
+GRID = [(1e-3, 1e-4), (1e-1, 1e-2), (1e-2, 1e-2)]
+
+
+@pytest.mark.parametrize("alpha,tau", GRID)
+@pytest.mark.parametrize("method", METHODS)
+def test_xstar_across_the_parameter_grid(c32, method, alpha, tau):
+    """x* against the oracle's at equal eps for other alpha and tau: within
+    1e-4, or within three times the oracle's own spread under float32-sized
+    perturbations of b (a stop decision one iteration earlier or later)."""
+    from gpu_util import oracle_spread
+    torch, s, prob, cfg = c32
+    p = oracle.Problem(A=prob.A, b=prob.b, n=prob.n, alpha=alpha, tau=tau)
+    x = torch.zeros(prob.N, device="cuda")
+    res = s.solve(method, dev_f32(torch, prob.b), alpha, tau, cfg.eps, x)
+    ref = ORACLE[method](p, np.zeros(prob.N), cfg.eps)
+    assert res.status == 0 and ref.status == 0
+    d = rel_l2(x.cpu().numpy(), ref.x)
+    if d > XSTAR_TOL:
+        _, spread = oracle_spread(p, ORACLE[method], cfg.eps)
+        assert d <= 3 * spread, (method, alpha, tau, d, spread, res.iters, ref.iters)
