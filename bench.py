@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
                     help="values of A: float32, or bfloat16 codes with per-row float32 scale")
     ap.add_argument("--pattern", default="solve",
-                    choices=["solve", "autograd", "batch", "paper", "grid"],
+                    choices=["solve", "autograd", "batch", "paper", "grid", "precision"],
                     help="autograd: phi forward + backward through torch.autograd at 128^3; "
-                         "grid: GP, GPBB and UPN over alpha x tau x eps at 64^3")
+                         "grid: GP, GPBB and UPN over alpha x tau x eps at 64^3; "
+                         "precision: GPBB and UPN at 256^3 with A stored three ways")
     return ap.parse_args()
 
 
@@ -601,6 +602,74 @@ def run_grid(args):
         "converged": sum(c["status"] == 0 for c in cases), "cases": cases}), flush=True)
 
 
+def run_precision(args):
+    """The storage-precision configuration: 256^3, 90 cone-beam views, 384^2
+    detector, 40 ellipsoids, 1% noise, alpha 1e-2, tau 1e-4; GPBB and UPN to
+    eps = 1e-5 (relative gradient-map stop) with A stored as FP32, as BF16
+    codes with per-row FP32 scales, and matrix-free.  The data b comes from the
+    FP32 system.  Reported per storage: build time, and per method the
+    iterations, time to eps, gradient evaluations/s and the relative L2
+    distance of x* from the FP32 storage's x*.  (Errors against the FP64
+    oracle per stage at this size: tests/test_gpu_precision.py with
+    TVR_PRECISION_FULL=1; the oracle cannot solve at this size.)"""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    cfg = synth.get_config("c256" if args.config == "c64" else args.config)
+    dev = torch.device("cuda", 0)
+    geom, x_true, z = make_problem(cfg, 0)
+    b = None
+    ref = {}
+    out = {}
+    opts = tvr.SolveOptions(k_max=5000)
+    for storage in ("fp32", "bf16", "mf"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sysm = tvr.System(geom, storage=storage)
+        torch.cuda.synchronize()
+        rec = {"build_ms": 1e3 * (time.perf_counter() - t0), "nnz": sysm.nnz}
+        if b is None:
+            xt = torch.tensor(x_true, dtype=torch.float32, device=dev)
+            ax = torch.empty(sysm.m, device=dev)
+            sysm.forward(xt, ax)
+            axh = ax.cpu().numpy().astype(np.float64)
+            b = torch.tensor((axh + cfg.noise * np.linalg.norm(axh) / math.sqrt(sysm.m) * z)
+                             .astype(np.float32), device=dev)
+            del xt, ax
+        x = torch.zeros(sysm.N, device=dev)
+        for method in ("gpbb", "upn"):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sysm.solve(method, b, cfg.alpha, cfg.tau, cfg.eps, x, opts)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t0)
+            xs = x.cpu().numpy().astype(np.float64)
+            m_rec = {"status": r.status, "iters": r.iters, "g_evals": r.g_evals, "ms": ms,
+                     "grad_evals_per_s": r.g_evals / (ms / 1e3), "phi": r.phi}
+            if storage == "fp32":
+                ref[method] = xs
+            else:
+                m_rec["rel_l2_to_fp32_xstar"] = float(np.linalg.norm(xs - ref[method])
+                                                      / np.linalg.norm(ref[method]))
+            rec[method] = m_rec
+        out[storage] = rec
+        del sysm, x
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "time to eps = 1e-5 (GPBB, UPN) at 256^3 with A stored as FP32, BF16 and "
+                  "matrix-free", "value": out["fp32"]["upn"]["ms"], "unit": "ms (UPN, FP32)",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"TV-CT {cfg.n}^3, cone beam {cfg.views} views x {cfg.det}^2 px, "
+                               f"{cfg.ellipsoids} seeded ellipsoids, 1% noise, alpha {cfg.alpha}, "
+                               f"tau {cfg.tau}, eps {cfg.eps}", "k_max": 5000},
+        "results": out}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -630,6 +699,10 @@ def main():
     if args.pattern == "grid":
         if rank == 0:
             run_grid(args)
+        return
+    if args.pattern == "precision":
+        if rank == 0:
+            run_precision(args)
         return
 
     import numpy as np
