@@ -299,8 +299,9 @@ TVR_API int tvr_solve_upn(const tvr_system *sys, const float *b, double alpha, d
 /*
  * Batch of independent problems (each its own system, data b, alpha and
  * x^(0) / x*): solves them with one method (1 = GP, 2 = GPBB, 3 = UPN) at the
- * same tau, eps and options, interleaved on one stream per system so that
- * small problems run concurrently on the GPU.  Arrays of `count` pointers
+ * same tau, eps and options, side by side on one stream per system (each
+ * stream relaunched as soon as its batch of passes drains) so that small
+ * problems run concurrently on the GPU.  Arrays of `count` pointers
  * (HOST arrays; the vectors they point to are host or device, as in the
  * single solves); a system may appear only once.  infos: nullable HOST array
  * of count records.  Synchronises `stream` at entry and every system's work
@@ -322,7 +323,10 @@ TVR_API int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t m
  * X holds k columns of N floats (column c at X + c*N, host or device):
  * x^(0) on entry, x* on return.  infos: nullable HOST array of k records
  * (phi is not evaluated: NaN).  Each column stops on its own test; a stopped
- * column is masked out of the later passes.  Synchronises `stream`.
+ * column is masked out of the later passes.  The row split of the two
+ * projections (lanes per row / column) is opts->sweep_lanes, or chosen by
+ * timing at the first sweep on a system of this shape (see tvr_solve_opts);
+ * infos report it.  Synchronises `stream`.
  * Returns TVR_OK if every column converged, else the first error status of a
  * column, else TVR_NOT_CONVERGED.  Not an entry of the paper: a batching of
  * its methods over alpha.

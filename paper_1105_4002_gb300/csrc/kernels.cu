@@ -8,7 +8,8 @@
 //               in UPN, the extrapolation y = x+ + beta (x+ - x) with its residual
 //               A y - b for the case of acceptance; GPBB forms two trial points
 //               (the second at the step a rejection leads to); the last block
-//               runs the test
+//               runs the test.  Rows and voxels are independent phases: odd
+//               warps run the voxels first
 //   k_backward  g = A^T r + alpha grad TV_tau(x) (CSC gather, atomic-free); plain
 //               modes fuse the TV_tau stencil and its value, the solver mode
 //               reads the TV gradient from the Huber weight planes and adds the
