@@ -135,17 +135,27 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def kernel_source_digest(paths) -> str:
+    """sha256 of the given C++/CUDA sources with comments and whitespace
+    removed: it changes with the code, not with its comments."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for name in paths:
+        with open(os.path.join(ROOT, name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update("".join(src.split()).encode())
+    return h.hexdigest()
+
+
 def captured_traffic(kernel: str, storage: str = "fp32"):
     """DRAM bytes per launch from the last ncu capture, if the kernels are unchanged since."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_64cubed.json")) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        for name in rec["kernel_sources"]:
-            with open(os.path.join(ROOT, name), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != rec["kernel_sources_sha256"]:
+        if kernel_source_digest(rec["kernel_sources"]) != rec["kernel_code_sha256"]:
             return None
         if storage != "fp32":
             return None

@@ -50,3 +50,13 @@ def test_bench_reads_no_undefined_name():
         _free_globals(child, free)
     missing = sorted(n for n in free if n not in defined and not hasattr(builtins, n))
     assert not missing, missing
+
+
+def test_kernel_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "k.cu").write_text("int f(int a) {\n  return a + 1;  // one\n}\n/* note */\n")
+    d0 = bench.kernel_source_digest(["k.cu"])
+    (tmp_path / "k.cu").write_text("// header\nint f(int a) {\n  return a + 1;  /* one */\n}\n")
+    assert bench.kernel_source_digest(["k.cu"]) == d0
+    (tmp_path / "k.cu").write_text("int f(int a) {\n  return a + 2;\n}\n")
+    assert bench.kernel_source_digest(["k.cu"]) != d0
