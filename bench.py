@@ -39,10 +39,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "grad-phi evals/s and time-to-eps (GPBB/UPN) at 64^3, % of HBM roofline, vs plain FP32"
 UNIT = "grad-phi evals/s"
-WORKLOAD = ("TV-CT 64^3, cone beam 25 views x 96^2 px (Dso 192, Dod 128), 10 seeded ellipsoids, "
-            "1% noise, alpha 1e-2, tau 1e-4; one GPBB + one UPN solve to relative "
-            "gradient-map norm 1e-4 from x0 = 0")
-L2_NOTE = "inputs larger than L2: A stored as CSR + CSC (2 x 156 MB) > 129 MB L2"
+L2_BYTES = 129e6
+
+
+def _e(v: float) -> str:
+    m, e = f"{v:.0e}".split("e")
+    return f"{m}e{int(e)}"
+
+
+def workload(cfg, eps) -> str:
+    """The bench workload of a configuration, in words."""
+    return (f"TV-CT {cfg.n}^3, cone beam {cfg.views} views x {cfg.det}^2 px (Dso {cfg.dso:g}, "
+            f"Dod {cfg.dod:g}), {cfg.ellipsoids} seeded ellipsoids, {cfg.noise * 100:g}% noise, "
+            f"alpha {_e(cfg.alpha)}, tau {_e(cfg.tau)}; one GPBB + one UPN solve to relative "
+            f"gradient-map norm {_e(eps)} from x0 = 0")
+
+
+def l2_note(nnz: int) -> str:
+    """Whether the stored matrix outgrows L2 (then no flush is needed between steps)."""
+    mb = 8 * nnz / 1e6
+    if 2 * 8 * nnz > L2_BYTES:
+        return f"inputs larger than L2: A stored as CSR + CSC (2 x {mb:.0f} MB) > 129 MB L2"
+    return (f"A stored as CSR + CSC (2 x {mb:.0f} MB) fits in the 129 MB L2: L2-resident between "
+            f"steps, not flushed")
+
+
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -150,14 +171,15 @@ def kernel_source_digest(paths) -> str:
     return h.hexdigest()
 
 
-def captured_traffic(kernel: str, storage: str = "fp32"):
-    """DRAM bytes per launch from the last ncu capture, if the kernels are unchanged since."""
+def captured_traffic(kernel: str, storage: str = "fp32", config: str = "c64"):
+    """DRAM bytes per launch from the last ncu capture, if it was taken on this
+    configuration and storage and the kernel code is unchanged since."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_64cubed.json")) as f:
             rec = json.load(f)
         if kernel_source_digest(rec["kernel_sources"]) != rec["kernel_code_sha256"]:
             return None
-        if storage != "fp32":
+        if storage != rec["storage"] or config != rec["config"]:
             return None
         return rec.get(kernel)
     except Exception:
@@ -220,13 +242,13 @@ def run_reference(args, cfg, eps):
     evals = sum(step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
     v = evals / dt
-    sample = (f"GPBB and UPN, first {k_sample} iterations each from x0 = 0 on the full 64^3 "
-              f"problem, per step ({evals} gradient evaluations in {dt:.1f} s)")
+    sample = (f"GPBB and UPN, first {k_sample} iterations each from x0 = 0 on the full "
+              f"{cfg.n}^3 problem, per step ({evals} gradient evaluations in {dt:.1f} s)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": cfg.n, "nnz": int(A.nnz),
+        "data": "synthetic", "config": {"workload": workload(cfg, eps), "n": cfg.n, "nnz": int(A.nnz),
                                         "parallelism": "single process, host cores"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -240,15 +262,22 @@ def cpu_baseline(cfg, eps, b_host, geom):
     A = oracle.system_matrix(geom)
     prob = oracle.Problem(A=A, b=b_host.astype(np.float64), n=cfg.n, alpha=cfg.alpha, tau=cfg.tau)
     x0 = np.zeros(prob.N)
-    k_sample = 8
-    t0 = time.perf_counter()
-    g = 0
-    for fn in (oracle.solve_gpbb, oracle.solve_upn):
-        g += fn(prob, x0, eps, oracle.Options(k_max=k_sample)).g_evals
-    dt = time.perf_counter() - t0
+
+    def sample(k):
+        t0 = time.perf_counter()
+        g = 0
+        for fn in (oracle.solve_gpbb, oracle.solve_upn):
+            g += fn(prob, x0, eps, oracle.Options(k_max=k)).g_evals
+        return g, time.perf_counter() - t0
+
+    # size the sample to about 12 s of CPU work from a 4-iteration calibration
+    g_cal, dt_cal = sample(4)
+    k_sample = int(min(2000, max(8, 12.0 / max(dt_cal / 4, 1e-6))))
+    g, dt = sample(k_sample)
     return {"value": g / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"GPBB and UPN, first {k_sample} iterations each on the same 64^3 problem "
-                      f"({g} gradient evaluations in {dt:.1f} s, FP64 numpy/scipy, one thread)"}
+            "sample": f"GPBB and UPN, first {k_sample} iterations each (or to eps) on the same "
+                      f"{cfg.n}^3 problem ({g} gradient evaluations in {dt:.1f} s, FP64 "
+                      f"numpy/scipy, one thread)"}
 
 
 # ------------------------------------------------------------- autograd
@@ -607,8 +636,8 @@ def run_grid(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else "bf16 values, f32 arithmetic",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": cfg.n, "views": cfg.views, "det": cfg.det,
-                   "storage": args.storage, "k_max": 20000},
+        "config": {"workload": workload(cfg, cfg.eps), "n": cfg.n, "views": cfg.views,
+                   "det": cfg.det, "storage": args.storage, "k_max": 20000},
         "converged": sum(c["status"] == 0 for c in cases), "cases": cases}), flush=True)
 
 
@@ -865,8 +894,8 @@ def main():
     bytes_fwd = w_share * fwd_g + (1 - w_share) * fwd_u
     bytes_bwd = w_share * bwd_g + (1 - w_share) * bwd_u
     # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
-    t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage)
-    t_u = captured_traffic("fwd_csr_trial_upn", args.storage)
+    t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage, args.config)
+    t_u = captured_traffic("fwd_csr_trial_upn", args.storage, args.config)
     trial_traffic = (w_share * t_g + (1 - w_share) * t_u) if (t_g and t_u) else None
     peak, peak_kind = measured_peak_gbs()
     roof = None
@@ -893,10 +922,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": cfg.n, "views": cfg.views, "det": cfg.det,
+        "config": {"workload": workload(cfg, eps), "n": cfg.n, "views": cfg.views, "det": cfg.det,
                    "m": m, "N": N, "nnz": nnz, "alpha": cfg.alpha, "tau": cfg.tau, "eps": eps,
                    "stop": "relative gradient-map norm", "methods": ["gpbb", "upn"],
-                   "l2": L2_NOTE, "passes_as_graphs": bool(args.graph), "storage": args.storage,
+                   "l2": l2_note(nnz), "passes_as_graphs": bool(args.graph), "storage": args.storage,
                    "parallelism": f"{world} independent problems (one per GPU)"},
         "time_to_eps": {"gpbb_ms": sorted(t_gpbb)[len(t_gpbb) // 2],
                         "upn_ms": sorted(t_upn)[len(t_upn) // 2],
