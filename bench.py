@@ -83,10 +83,13 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
                     help="values of A: float32, or bfloat16 codes with per-row float32 scale")
     ap.add_argument("--pattern", default="solve",
-                    choices=["solve", "autograd", "batch", "paper", "grid", "precision"],
+                    choices=["solve", "autograd", "batch", "paper", "grid", "precision", "sweep"],
                     help="autograd: phi forward + backward through torch.autograd at 128^3; "
                          "grid: GP, GPBB and UPN over alpha x tau x eps at 64^3; "
-                         "precision: GPBB and UPN at 256^3 with A stored three ways")
+                         "precision: GPBB and UPN at 256^3 with A stored three ways; "
+                         "sweep: one 8-alpha sweep at 128^3 (--sweep-kmax iterations)")
+    ap.add_argument("--sweep-kmax", type=int, default=20000,
+                    help="iteration cap of the sweep pattern (a short run for profiling)")
     return ap.parse_args()
 
 
@@ -710,6 +713,44 @@ def run_precision(args):
         "results": out}), flush=True)
 
 
+def run_sweep(args):
+    """One 8-alpha UPN sweep (1e-4 .. 1e-1, log-spaced) sharing A at 128^3 /
+    60 views / 192^2, FP32 storage, to eps = 1e-4 or --sweep-kmax iterations
+    (a short run to profile the sweep's kernels); passes per second."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    cfg = synth.get_config("c128")
+    dev = torch.device("cuda", 0)
+    sysm = tvr.System(cfg.geometry(), storage=args.storage)
+    xt = torch.tensor(cfg.phantom(), dtype=torch.float32, device=dev)
+    ax = torch.empty(sysm.m, device=dev)
+    sysm.forward(xt, ax)
+    axh = ax.cpu().numpy().astype(np.float64)
+    z = synth.standard_normal(sysm.m, cfg.seed + 1000)
+    b = torch.tensor((axh + cfg.noise * np.linalg.norm(axh) / math.sqrt(sysm.m) * z)
+                     .astype(np.float32), device=dev)
+    X = torch.zeros(8 * sysm.N, device=dev)
+    opts = tvr.SolveOptions(k_max=args.sweep_kmax)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs = sysm.solve_sweep("upn", b, list(np.logspace(-4, -1, 8)), cfg.tau, 1e-4, X, opts)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "passes/s of an 8-alpha UPN sweep at 128^3", "value": rs[0].passes / dt,
+        "unit": "passes/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "TV-CT 128^3, cone beam 60 views x 192^2 px, 20 ellipsoids, 0.5% "
+                               "noise, alpha 1e-4 .. 1e-1 (8, log-spaced), tau 1e-4, eps 1e-4",
+                   "k_max": args.sweep_kmax, "storage": args.storage, "nnz": sysm.nnz},
+        "iters": [r.iters for r in rs], "passes": rs[0].passes, "ms": 1e3 * dt,
+        "lanes_rows_cols": list(rs[0].lanes)}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -743,6 +784,10 @@ def main():
     if args.pattern == "precision":
         if rank == 0:
             run_precision(args)
+        return
+    if args.pattern == "sweep":
+        if rank == 0:
+            run_sweep(args)
         return
 
     import numpy as np
