@@ -2,13 +2,10 @@
 each kernel (against the counts of the 64^3 bench problem: m = 230,400 rays,
 N = 64^3 voxels, nnz = 19,477,604) and the digest that keys the captured
 traffic to the kernel code."""
-import os
-
 import pytest
 
 import bench
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 M, N, NNZ = 230_400, 64 ** 3, 19_477_604
 
 
