@@ -88,3 +88,35 @@ def test_defaults_and_argument_errors_without_gpu(built):
         _capi.TVR_ERR_ARG
     assert L.tvr_solve_upn(None, None, 0.0, 1.0, 1.0, None, None, None, None) == _capi.TVR_ERR_ARG
     assert b"null" in L.tvr_last_error()
+
+
+def test_more_validation_without_gpu(built):
+    """Option defaults added to the ABI, and argument checks that run before
+    any device call: unknown storage, non-finite views, a grid too large for
+    int32 voxel indices, null batch and sweep arguments."""
+    import ctypes
+    import numpy as np
+    import paper_1105_4002_gb300 as pkg
+    from paper_1105_4002_gb300 import _capi
+    L = pkg.lib()
+    o = _capi.SolveOpts()
+    L.tvr_solve_opts_default(ctypes.byref(o))
+    assert (o.gpbb_points, o.sweep_lanes, o.batch, o.use_graph) == (2, 0, 32, 1)
+    h = ctypes.c_void_p()
+    views = np.zeros((1, 12), np.float64)
+    g = _capi.Geometry(4, 1, 4, 4, _capi.TVR_CONE, 0, views.ctypes.data)
+    assert L.tvr_build_system(ctypes.byref(g), 7, None, ctypes.byref(h)) == _capi.TVR_ERR_ARG
+    assert b"storage" in L.tvr_last_error()
+    views[0, 3] = np.nan
+    assert L.tvr_build_system(ctypes.byref(g), 0, None, ctypes.byref(h)) == _capi.TVR_ERR_ARG
+    assert b"non-finite" in L.tvr_last_error()
+    views[0, 3] = 0.0
+    big = _capi.Geometry(1291, 1, 4, 4, _capi.TVR_CONE, 0, views.ctypes.data)  # 1291^3 > 2^31
+    assert L.tvr_build_system(ctypes.byref(big), 0, None, ctypes.byref(h)) == _capi.TVR_ERR_ARG
+    assert b"2^31" in L.tvr_last_error()
+    assert L.tvr_solve_batch(None, 0, 3, None, None, 1e-4, 1e-4, None, None, None, None) == \
+        _capi.TVR_ERR_ARG
+    assert L.tvr_solve_sweep(None, 3, None, None, 1, 1e-4, 1e-4, None, None, None, None) == \
+        _capi.TVR_ERR_ARG
+    for code in (_capi.TVR_OK, _capi.TVR_NOT_CONVERGED, _capi.TVR_ERR_ARG):
+        assert L.tvr_status_str(code)
