@@ -359,6 +359,13 @@ def run_autograd(args):
 
 
 # ------------------------------------------------------ paper experiment
+# The experiment of the paper's Sec. IV as printed there (tests/golden/paper_printed_values.txt);
+# tau is this implementation's smoothing (the paper does not print one).
+PAPER_EXPERIMENT = {"n": 64, "views": (55, 19), "det": 91, "noise": 0.01, "alpha": 1e-2,
+                    "tau": 1e-4, "eps": 1e-8, "phi_star_eps_factor": 1e-2,
+                    "checkpoints": (10, 30, 100, 300, 1000, 2000)}
+
+
 def run_paper(args):
     """The convergence comparison of the paper's Sec. IV on its scan shape: a
     64^3 volume, parallel beam with view directions spread evenly over the
@@ -379,21 +386,23 @@ def run_paper(args):
     from paper_1105_4002_gb300 import SolveOptions
     from paper_1105_4002_gb300._capi import TVR_STOP_PER_N
     dev = torch.device("cuda", 0)
-    n, det, alpha, tau, eps = 64, 91, 1e-2, 1e-4, 1e-8
-    checkpoints = [10, 30, 100, 300, 1000, 2000]
+    P = PAPER_EXPERIMENT
+    n, det, alpha, tau, eps = P["n"], P["det"], P["alpha"], P["tau"], P["eps"]
+    checkpoints = list(P["checkpoints"])
     x_true = synth.ellipsoid_phantom(n, 10, (4.0, 20.0), (0.0, 1.0), 6)
     results = {}
     sampler = ClockSampler(gpu_id_for(torch, dev))
     sampler.start()
     t_all = time.perf_counter()
-    for label, views in (("many_view_55", 55), ("few_view_19", 19)):
+    for label, views in ((f"many_view_{P['views'][0]}", P["views"][0]),
+                         (f"few_view_{P['views'][1]}", P["views"][1])):
         geom = synth.sphere_parallel_geometry(n, views, det)
         s = tvr.System(geom)
         xt = torch.tensor(x_true, dtype=torch.float32, device=dev)
         ax = torch.empty(geom.m, dtype=torch.float32, device=dev)
         s.forward(xt, ax)
         axh = ax.cpu().numpy().astype(np.float64)
-        e = synth.noise_exact(axh, synth.standard_normal(geom.m, 600 + views), 0.01)
+        e = synth.noise_exact(axh, synth.standard_normal(geom.m, 600 + views), P["noise"])
         b = torch.tensor((axh + e).astype(np.float32), device=dev)
 
         def phi_of(x):
@@ -409,7 +418,7 @@ def run_paper(args):
             torch.cuda.synchronize()
             return r, x, 1e3 * (time.perf_counter() - t0)
 
-        r_star, x_star, _ = solve("upn", eps / 100, 20000)
+        r_star, x_star, _ = solve("upn", eps * P["phi_star_eps_factor"], 20000)
         phi_star = phi_of(x_star)
         per = {"rows_m": geom.m, "unknowns_N": geom.N, "rows_below_unknowns": geom.m < geom.N,
                "phi_star": phi_star, "phi_star_upn_iters": r_star.iters,
