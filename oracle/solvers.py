@@ -53,6 +53,10 @@ class Options:
     mu_bar: float | None = None  # None -> 0.1 * L_bar
     bt_max: int = 60
     record: bool = False
+    # with record: also keep, per iteration, copies of the vectors the step's
+    # scalars came from (GPBB: x^(k) and grad f(x^(k)); UPN: the pair
+    # (x^(k), y^(k)) of the mu-estimate), so that tests can recompute them
+    record_iterates: bool = False
 
 
 @dataclasses.dataclass
@@ -202,6 +206,8 @@ def solve_gpbb(prob: Problem, x0, eps: float, opts: Options | None = None) -> Re
         fhist.append(f)
         if opts.record:
             hist.append(dict(k=k, f=f, gnorm=gnorm, theta=theta, beta=beta, trials=trials))
+            if opts.record_iterates:
+                hist[-1].update(x=x_prev.copy(), g=g_prev.copy())
         if not (math.isfinite(f) and math.isfinite(gnorm)):
             status = ERR_NONFINITE
             break
@@ -255,11 +261,14 @@ def solve_upn(prob: Problem, x0, eps: float, opts: Options | None = None) -> Res
             theta_new = upn_theta_next(theta, mu / L)
             beta = theta * (1.0 - theta) / (theta * theta + theta_new)
             gnorm = L * float(np.linalg.norm(y - x_new))                   # G_{L_k}(y(k))
+            pair = (xk, y)
             y = x_new + beta * (x_new - xk)
             xk, fk, theta = x_new, f_new, theta_new
             if opts.record:
                 hist.append(dict(k=k, f=fk, gnorm=gnorm, L=L, mu=mu, theta=theta, beta=beta,
                                  trials=j))
+                if opts.record_iterates:
+                    hist[-1].update(x=pair[0].copy(), y=pair[1].copy())
             if not (math.isfinite(fk) and math.isfinite(gnorm)):
                 status = ERR_NONFINITE
                 break
