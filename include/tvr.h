@@ -175,20 +175,27 @@ TVR_API int tvr_phi_vjp_f64(const tvr_system *sys, const double *x, const double
 
 /*
  * tvr_phi_and_grad without any device allocation (the paper has no
- * counterpart: this serves callers that cannot allocate while they evaluate
- * phi -- code recording a CUDA stream capture, code whose device memory is
- * owned by another framework's allocator, real-time loops that must not enter
- * the driver's allocator).  Same kernels and results as tvr_phi_and_grad
- * (no resid output).  Its scratch -- the residual and the reduction
- * partials -- is one fixed device array inside the library (about 16.4 MiB,
- * held on every GPU that loads the library until the process exits), so:
+ * counterpart).  For callers that must not allocate device memory while they
+ * evaluate phi: code whose device memory is owned by another framework's
+ * caching allocator under a fixed budget (an allocation outside that
+ * allocator can fail, or fragment what the allocator manages), and
+ * latency-bound loops that must not enter the driver's allocator (cudaMalloc
+ * and cudaFree can synchronise the device and take unbounded time).  Same
+ * kernels and results as tvr_phi_and_grad (no resid output).  Its scratch --
+ * the residual and three reduction slots -- is one fixed device array inside
+ * the library, about 17.5 MiB (16 MiB residual, 1.5 MiB reductions), held on
+ * every GPU that loads the library until the process exits, so:
  *   - the system's rays m must be <= 4,194,304, else TVR_ERR_ARG;
+ *   - the system must store A as FP32 CSR or be matrix-free; BF16 row-scale
+ *     storage needs a second, row-scaled residual and is refused (TVR_ERR_ARG);
  *   - x, b (and grad, phi_dev when given) must be DEVICE memory (host data
  *     would need staging buffers), else TVR_ERR_ARG;
- *   - the first call on a device looks up the array's device address; make
- *     that first call before any stream capture;
- *   - every call shares the array: calls whose work overlaps on the GPU
- *     (other streams, other threads) race; order them on one stream.
+ *   - the first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture;
+ *   - every call shares the array and zeroes its reduction counters first:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race; order them on one stream.
  * phi_dev / phi_host as in tvr_phi_and_grad (phi_host synchronises).
  */
 TVR_API int tvr_phi_and_grad_noalloc(const tvr_system *sys, const float *x, const float *b,

@@ -1,14 +1,15 @@
 // phi and grad phi without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they evaluate the
-// objective: code recording a CUDA stream capture (a cudaMalloc there is not
-// part of the captured work and breaks or invalidates the capture), code
-// running under a fixed memory budget owned by another framework's caching
-// allocator, or a real-time loop that must not enter the driver's allocator.
-// tvr_phi_and_grad_noalloc serves them.  It runs the same kernels as
-// tvr_phi_and_grad, but its scratch -- the residual vector and the
-// reduction partials, counters and results -- lives in one file-scope device
-// array of fixed size instead of the system's lazily allocated workspace.
+// Some callers must not allocate device memory at the moment they evaluate
+// the objective: code whose device memory is owned by another framework's
+// caching allocator under a fixed budget (an allocation outside it can fail
+// or fragment what that allocator manages), and latency-bound loops that must
+// not enter the driver's allocator (cudaMalloc / cudaFree can synchronise the
+// device and take unbounded time).  tvr_phi_and_grad_noalloc serves them.  It
+// runs the same kernels as tvr_phi_and_grad, but its scratch -- the residual
+// vector and the reduction partials, counters and results -- lives in one
+// file-scope device array of fixed size instead of the system's lazily
+// allocated workspace.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,13 +22,14 @@ namespace {
 // Largest residual (rays) the static scratch holds.
 constexpr int64_t kNoallocMaxRows = (int64_t)1 << 22;  // 4,194,304 rays = 16 MiB
 
-constexpr size_t kPartBytes = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;  // per reduction slot
+constexpr size_t kPartBytes = sizeof(FF) * TVR_MAX_GRID * TVR_RMAX;  // 512 KiB per reduction slot
 constexpr size_t kCounterBytes = 256;                                 // per slot, zeroed per call
 constexpr size_t kOutBytes = 256;                                     // per slot
 constexpr int kNoallocSlots = 3;                                      // forward, backward, TV value
 constexpr size_t kPhiBytes = 256;
 constexpr size_t kScratchBytes = kNoallocSlots * (kPartBytes + kCounterBytes + kOutBytes) +
                                  kPhiBytes + sizeof(float) * kNoallocMaxRows;
+static_assert(kScratchBytes < ((size_t)18 << 20), "the documented size is about 17.5 MiB");
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -59,8 +61,12 @@ extern "C" int tvr_phi_and_grad_noalloc(const tvr_system *sys, const float *x, c
   if (!sys || !x || !b) return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: null argument");
   if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
     return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: need alpha >= 0 and tau > 0");
-  if (sys->A.storage != TVR_STORAGE_FP32)
-    return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: needs a system with FP32 storage");
+  // BF16 row-scale storage gathers a second, row-scaled residual in the back
+  // projection, which the static scratch does not hold
+  if (sys->A.storage != TVR_STORAGE_FP32 && sys->A.storage != TVR_STORAGE_MATRIX_FREE)
+    return tvr_fail(TVR_ERR_ARG,
+                    "tvr_phi_and_grad_noalloc: needs FP32 or matrix-free storage (BF16 row-scale "
+                    "storage would need a second residual)");
   if (sys->m > kNoallocMaxRows)
     return tvr_fail(TVR_ERR_ARG,
                     "tvr_phi_and_grad_noalloc: the system has more rays than the static scratch "

@@ -624,9 +624,17 @@ int sweep_tune(const MatDev &A, int device, const SweepBufs &B, const SweepDev *
   TVR_CUDA(cudaMemsetAsync(B.XB, 0, sizeof(float) * KS * A.N, s));
   TVR_CUDA(cudaMemsetAsync(B.DD, 0, sizeof(float) * KS * A.N, s));
   TVR_CUDA(cudaMemsetAsync(B.RG, 0, sizeof(float) * KS * A.m, s));
-  cudaEvent_t e0, e1;
-  TVR_CUDA(cudaEventCreate(&e0));
-  TVR_CUDA(cudaEventCreate(&e1));
+  // destroyed on every exit path, including the early returns of TVR_CUDA
+  struct Events {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t v : e)
+        if (v) cudaEventDestroy(v);
+    }
+  } ev;
+  TVR_CUDA(cudaEventCreate(&ev.e[0]));
+  TVR_CUDA(cudaEventCreate(&ev.e[1]));
+  cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
   auto timed = [&](auto launch, float *ms) -> int {
     launch();
     TVR_CUDA(cudaEventRecord(e0, s));
@@ -661,8 +669,6 @@ int sweep_tune(const MatDev &A, int device, const SweepBufs &B, const SweepDev *
     return cand[best];
   };
   const int lr = pick(tr), lc = pick(tc);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (rc != TVR_OK) return rc;
   std::lock_guard<std::mutex> lk(mu);
   cache[key] = {lr, lc};

@@ -1,11 +1,12 @@
 """tvr_phi_and_grad_noalloc against tvr_phi_and_grad, through the C ABI.
 
-The no-allocation variant exists for callers that cannot allocate device
-memory while they evaluate phi: code recording a CUDA stream capture, code
-whose device memory belongs to another framework's allocator, and real-time
-loops that must stay out of the driver's allocator.  It must give the same
-phi and gradient as the ordinary entry point, on consecutive calls that share
-its fixed scratch array, and refuse what its scratch cannot hold.
+The no-allocation variant exists for callers that must not allocate device
+memory while they evaluate phi: code whose device memory belongs to another
+framework's caching allocator under a fixed budget, and latency-bound loops
+that must stay out of the driver's allocator (which can synchronise the
+device).  It must give the same phi and gradient as the ordinary entry point,
+on consecutive calls that share its fixed scratch array, for stored FP32 and
+matrix-free systems, and refuse what its scratch cannot hold.
 """
 import ctypes
 
@@ -37,11 +38,12 @@ def _noalloc(s, x, b, alpha, tau, grad, stream):
     return st, (out[0], out[1], out[2])
 
 
-def test_noalloc_matches_phi_and_grad_on_consecutive_calls():
+@pytest.mark.parametrize("storage", ["fp32", "mf"])
+def test_noalloc_matches_phi_and_grad_on_consecutive_calls(storage):
     torch = cuda()
     from paper_1105_4002_gb300 import System
     geom = synth.get_config("c32").geometry()
-    s = System(geom)
+    s = System(geom, storage=storage)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rng = np.random.default_rng(4)
     b = torch.tensor(rng.uniform(0, 5, geom.m), dtype=torch.float32, device="cuda")
@@ -73,8 +75,15 @@ def test_noalloc_refuses_what_its_scratch_cannot_hold():
     st, _ = _noalloc(s, x, b, 1e-2, 1e-4, g, stream)
     assert st == -1
     assert b"static scratch" in lib().tvr_last_error()
+    # BF16 row-scale storage would need a second, row-scaled residual
+    geom8 = synth.get_config("c8").geometry()
+    s16 = System(geom8, storage="bf16")
+    x8 = torch.zeros(geom8.N, device="cuda")
+    b8 = torch.zeros(geom8.m, device="cuda")
+    st, _ = _noalloc(s16, x8, b8, 1e-2, 1e-4, torch.empty(geom8.N, device="cuda"), stream)
+    assert st == -1 and b"BF16" in lib().tvr_last_error()
     # host memory would need staging buffers
-    small = System(synth.get_config("c8").geometry())
+    small = System(geom8)
     xh = np.zeros(small.N, np.float32)
     bh = np.zeros(small.m, np.float32)
     st = lib().tvr_phi_and_grad_noalloc(small.handle, xh.ctypes.data_as(ctypes.c_void_p),
