@@ -90,6 +90,11 @@ def parse():
                          "sweep: one 8-alpha sweep at 128^3 (--sweep-kmax iterations)")
     ap.add_argument("--sweep-kmax", type=int, default=20000,
                     help="iteration cap of the sweep pattern (a short run for profiling)")
+    ap.add_argument("--roofline-steps", type=int, default=3,
+                    help="extra steps after the timed region in which the dominant kernels "
+                         "are timed with CUDA events")
+    ap.add_argument("--cpu-baseline-b", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-baseline-kmax", type=int, default=20000, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -220,6 +225,21 @@ def make_problem(cfg, rank):
     return geom, x_true, z
 
 
+def bench_config(cfg, eps, nnz, storage, graph, world):
+    """The `config` of the bench line; both arms print the same dict."""
+    return {"workload": workload(cfg, eps), "n": cfg.n, "views": cfg.views, "det": cfg.det,
+            "m": cfg.views * cfg.det * cfg.det, "N": cfg.n ** 3, "nnz": int(nnz),
+            "alpha": cfg.alpha, "tau": cfg.tau, "eps": eps, "stop": "relative gradient-map norm",
+            "methods": ["gpbb", "upn"], "l2": l2_note(nnz), "passes_as_graphs": bool(graph),
+            "storage": storage, "parallelism": f"{world} independent problems (one per GPU)"}
+
+
+DATA_NOTE = ("b = A x_true + e, e = 0.01 ||A x_true|| / sqrt(m) z (z seeded standard normal), "
+             "rounded to float32; each arm forms A x_true with its own projector (the GPU arm "
+             "in float32 on the device, the CPU oracle in float64), so the two b agree to float32 "
+             "rounding")
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args, cfg, eps):
     """FP64 CPU oracle on the same workload; each step a bounded sample."""
@@ -245,43 +265,77 @@ def run_reference(args, cfg, eps):
     evals = sum(step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
     v = evals / dt
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     sample = (f"GPBB and UPN, first {k_sample} iterations each from x0 = 0 on the full "
-              f"{cfg.n}^3 problem, per step ({evals} gradient evaluations in {dt:.1f} s)")
+              f"{cfg.n}^3 problem, per step ({evals} gradient evaluations in {dt:.1f} s, FP64 "
+              f"numpy/scipy, one thread of {os.cpu_count()})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload(cfg, eps), "n": cfg.n, "nnz": int(A.nnz),
-                                        "parallelism": "single process, host cores"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "data_note": DATA_NOTE,
+        "config": bench_config(cfg, eps, A.nnz, args.storage, args.graph, world),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "nproc": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(cfg, eps, b_host, geom):
-    """The oracle as it stands on a bounded sample of the bench workload."""
+def cpu_baseline_leg(args, cfg, eps):
+    """Run in a child process (no CUDA): the oracle as it stands solving the
+    bench problem to eps with GPBB and with UPN from x0 = 0, with the b the GPU
+    arm used (read from --cpu-baseline-b).  Prints one JSON object."""
     import numpy as np
     import oracle
+    geom, _, _ = make_problem(cfg, 0)
+    b = np.load(args.cpu_baseline_b).astype(np.float64)
     A = oracle.system_matrix(geom)
-    prob = oracle.Problem(A=A, b=b_host.astype(np.float64), n=cfg.n, alpha=cfg.alpha, tau=cfg.tau)
+    prob = oracle.Problem(A=A, b=b, n=cfg.n, alpha=cfg.alpha, tau=cfg.tau)
     x0 = np.zeros(prob.N)
-
-    def sample(k):
+    out = {}
+    g_total, t_total = 0, 0.0
+    for name, fn in (("gpbb", oracle.solve_gpbb), ("upn", oracle.solve_upn)):
         t0 = time.perf_counter()
-        g = 0
-        for fn in (oracle.solve_gpbb, oracle.solve_upn):
-            g += fn(prob, x0, eps, oracle.Options(k_max=k)).g_evals
-        return g, time.perf_counter() - t0
+        r = fn(prob, x0, eps, oracle.Options(k_max=args.cpu_baseline_kmax))
+        dt = time.perf_counter() - t0
+        out[name] = {"status": r.status, "iters": r.iters, "g_evals": r.g_evals,
+                     "f_evals": r.f_evals, "s": dt}
+        g_total += r.g_evals
+        t_total += dt
+    print(json.dumps({"evals": g_total, "s": t_total, "solves": out, "nproc": os.cpu_count()}),
+          flush=True)
 
-    # size the sample to 10-20 s of CPU work from a 4-iteration calibration (the
-    # first iterations are the cheap ones: the target is set above the aim)
-    g_cal, dt_cal = sample(4)
-    k_sample = int(min(2000, max(8, 18.0 / max(dt_cal / 4, 1e-6))))
-    g, dt = sample(k_sample)
-    return {"value": g / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"GPBB and UPN, first {k_sample} iterations each (or to eps) on the same "
-                      f"{cfg.n}^3 problem ({g} gradient evaluations in {dt:.1f} s, FP64 "
-                      f"numpy/scipy, one thread)"}
+
+def cpu_baseline(cfg, eps, b_host, storage):
+    """The oracle as it stands, timed in a child process on the host cores:
+    one GPBB and one UPN solve of the bench problem to eps (time-to-eps, FP64
+    numpy/scipy, one thread)."""
+    import tempfile
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "b.npy")
+        np.save(path, b_host)
+        cmd = [sys.executable, os.path.abspath(__file__), "--config", cfg.name, "--eps", repr(eps),
+               "--storage", storage, "--cpu-baseline-b", path]
+        env = dict(os.environ)
+        for v in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+            env.pop(v, None)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        p = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if p.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"failed: {p.stderr.strip()[-300:]}"}
+    rec = json.loads(p.stdout.strip().splitlines()[-1])
+    sv = rec["solves"]
+    return {"value": rec["evals"] / rec["s"], "unit": UNIT, "cores": 1, "nproc": rec["nproc"],
+            "kind": "oracle",
+            "time_to_eps": {"gpbb_s": sv["gpbb"]["s"], "upn_s": sv["upn"]["s"],
+                            "gpbb_iters": sv["gpbb"]["iters"], "upn_iters": sv["upn"]["iters"],
+                            "status": [sv["gpbb"]["status"], sv["upn"]["status"]]},
+            "sample": f"one GPBB and one UPN solve of the same {cfg.n}^3 problem to eps from "
+                      f"x0 = 0 with the GPU arm's b ({rec['evals']} gradient evaluations in "
+                      f"{rec['s']:.1f} s; FP64 numpy/scipy, one thread of {rec['nproc']}; child "
+                      f"process)"}
 
 
 # ------------------------------------------------------------- autograd
@@ -475,6 +529,26 @@ def solver_launch_bytes(m: int, N: int, nnz: int, storage: str, method: str):
     fwd = (4 + vb) * nnz + 8 * (m + 1) + 8 * N + 4 * N + 2 * 4 * m + extra_m * m
     fwd += {"gpbb": 16 * N + 4 * m + 20 * N, "upn": 12 * m + 24 * N, "gp": 16 * N}[method]
     return bwd, fwd
+
+
+def trial_bytes(m: int, N: int, nnz: int, storage: str, method: str) -> float:
+    """Algorithmic bytes of one working trial launch, per unit as the scope
+    table's measurement row counts them: the f-only trial 8 nnz + 12 m + 8 N
+    (values and indices of A, b read and r written and gathered, the gathered
+    point), 12 B per voxel for the projected step (A5) and, in UPN, 12 B per
+    voxel for the extrapolation (A8).  BF16 storage: 6 B per entry."""
+    per_entry = 8 if storage == "fp32" else 6
+    b = per_entry * nnz + 12 * m + 8 * N + 12 * N
+    if method == "upn":
+        b += 12 * N
+    return float(b)
+
+
+def backprojection_bytes(m: int, N: int, nnz: int, storage: str) -> float:
+    """Algorithmic bytes of one working back projection: A^T (8 B per entry,
+    6 with BF16 values), r read, x read and g written."""
+    per_entry = 8 if storage == "fp32" else 6
+    return float(per_entry * nnz + 4 * m + 8 * N)
 
 
 def plain_launch_bytes(m: int, N: int, nnz: int, storage: str):
@@ -770,6 +844,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.cpu_baseline_b:
+        cpu_baseline_leg(args, cfg, eps)
+        return
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, cfg, eps)
@@ -845,13 +922,8 @@ def main():
         step(b, xg, xu)
     torch.cuda.synchronize()
 
-    # ---- timed region ----
+    # ---- timed region (no kernel timing inside: the graphs replay as they are) ----
     sampler = ClockSampler(gpu_id_for(torch, dev))
-    # the timed region times only the dominant kernel (the trial forward
-    # projection), on every 32nd pass: event nodes around every kernel would
-    # slow the graphs
-    sysm.profile(True, kinds=("forward",), sample_stride=32)
-    sysm.profile_read()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -860,7 +932,6 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
     evals = 0
-    passes = 0
     launches = 0
     passes_gpbb = passes_upn = 0
     t_gpbb, t_upn, it_gpbb, it_upn = [], [], [], []
@@ -875,21 +946,30 @@ def main():
         it_gpbb.append(r1.iters)
         it_upn.append(r2.iters)
         evals += r1.g_evals + r2.g_evals
-        passes += r1.passes + r2.passes
         passes_gpbb += r1.passes
         passes_upn += r2.passes
-        # init (2) + per pass (2 GPBB / 3 UPN: the step is fused into the trial forward)
-        # + final phi (2)
-        launches += 2 + 2 * r1.passes + 2 + 2 + 3 * r2.passes + 2
+        # per solve: the initial phi and gradient (2), two kernels per pass
+        # (back projection, trial), phi at x* (forward + TV value, 2)
+        launches += (2 + 2 * r1.passes + 2) + (2 + 2 * r2.passes + 2)
     ev1.record()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
+
+    # ---- roofline pass: the same solves again, after the timed region, with
+    # CUDA event nodes around the trial and back-projection kernels of every
+    # 4th pass (launches that did work only) ----
+    sysm.profile(True, kinds=("forward", "backward"), sample_stride=4)
+    sysm.profile_read()
+    rp_gpbb = rp_upn = 0
+    for _ in range(max(args.roofline_steps, 1)):
+        rp_gpbb += sysm.solve("gpbb", b, cfg.alpha, cfg.tau, eps, xg.zero_(), opts).passes
+        rp_upn += sysm.solve("upn", b, cfg.alpha, cfg.tau, eps, xu.zero_(), opts).passes
     prof = sysm.profile_read()
     sysm.profile(False)
-    # per-kernel breakdown: one more step with every kernel timed (outside the timed region)
+    # per-kernel breakdown: one more step with every kernel timed
     sysm.profile(True)
     sysm.profile_read()
     sysm.solve("gpbb", b, cfg.alpha, cfg.tau, eps, xg.zero_(), opts)
@@ -943,18 +1023,19 @@ def main():
         return
 
     m, N, nnz = geom.m, geom.N, sysm.nnz
-    w_share = passes_gpbb / max(passes_gpbb + passes_upn, 1)
-    bwd_g, fwd_g = solver_launch_bytes(m, N, nnz, args.storage, "gpbb")
-    bwd_u, fwd_u = solver_launch_bytes(m, N, nnz, args.storage, "upn")
-    bytes_fwd = w_share * fwd_g + (1 - w_share) * fwd_u
-    bytes_bwd = w_share * bwd_g + (1 - w_share) * bwd_u
-    # DRAM bytes of the captured GP/GPBB and UPN trial launches, mixed like bytes_fwd
+    w_share = rp_gpbb / max(rp_gpbb + rp_upn, 1)
+    bytes_fwd = w_share * trial_bytes(m, N, nnz, args.storage, "gpbb") + \
+        (1 - w_share) * trial_bytes(m, N, nnz, args.storage, "upn")
+    bytes_bwd = backprojection_bytes(m, N, nnz, args.storage)
+    # DRAM bytes of the captured GPBB and UPN trial launches, mixed like bytes_fwd
     t_g = captured_traffic("fwd_csr_trial_gpbb", args.storage, args.config)
     t_u = captured_traffic("fwd_csr_trial_upn", args.storage, args.config)
     trial_traffic = (w_share * t_g + (1 - w_share) * t_u) if (t_g and t_u) else None
+    bwd_traffic = captured_traffic("bwd_csc_tv", args.storage, args.config)
     peak, peak_kind = measured_peak_gbs()
     roof = None
     nf, msf = prof["forward"]
+    nb, msb = prof["backward"]
     if nf:
         avg_s = msf / nf / 1e3
         ach = bytes_fwd / avg_s / 1e9
@@ -962,12 +1043,19 @@ def main():
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": trial_traffic, "kernel": "fwd_csr_trial",
                 "launches": nf, "avg_us": 1e6 * avg_s, "algorithmic_bytes_per_launch": bytes_fwd,
+                "bytes_rule": "per unit as in the scope table's measurement row: f-only trial "
+                              "8 nnz + 12 m + 8 N, plus 12 B per voxel for the projected step "
+                              "and, in UPN, 12 B per voxel for the extrapolation",
                 "peak_source": peak_kind,
-                "timing": "CUDA event nodes around the kernel in every 32nd pass of the timed "
-                          "region (launches that did work only)",
+                "timing": f"separate pass after the timed region ({max(args.roofline_steps, 1)} "
+                          "steps): CUDA event nodes around the kernel in every 4th pass, "
+                          "launches that did work only",
+                "backprojection": ({"avg_us": 1e3 * msb / nb, "launches": nb,
+                                    "algorithmic_bytes_per_launch": bytes_bwd,
+                                    "achieved": bytes_bwd / (msb / nb / 1e3) / 1e9,
+                                    "frac": bytes_bwd / (msb / nb / 1e3) / 1e9 / peak,
+                                    "traffic": bwd_traffic} if nb else None),
                 "breakdown_us": bk,
-                "breakdown_frac": {"forward": bytes_fwd / (bk["forward"] / 1e6) / 1e9 / peak,
-                                   "backward": bytes_bwd / (bk["backward"] / 1e6) / 1e9 / peak},
                 "breakdown_note": "per-launch means of one extra step with every kernel timed "
                                   "(event nodes around each kernel slow the small ones); the "
                                   "projected step runs inside the trial forward kernel"}
@@ -977,11 +1065,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload(cfg, eps), "n": cfg.n, "views": cfg.views, "det": cfg.det,
-                   "m": m, "N": N, "nnz": nnz, "alpha": cfg.alpha, "tau": cfg.tau, "eps": eps,
-                   "stop": "relative gradient-map norm", "methods": ["gpbb", "upn"],
-                   "l2": l2_note(nnz), "passes_as_graphs": bool(args.graph), "storage": args.storage,
-                   "parallelism": f"{world} independent problems (one per GPU)"},
+        "data_note": DATA_NOTE,
+        "config": bench_config(cfg, eps, nnz, args.storage, args.graph, world),
         "time_to_eps": {"gpbb_ms": sorted(t_gpbb)[len(t_gpbb) // 2],
                         "upn_ms": sorted(t_upn)[len(t_upn) // 2],
                         "gpbb_iters": it_gpbb[-1], "upn_iters": it_upn[-1],
@@ -997,7 +1082,7 @@ def main():
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, eps, b_host, geom)
+        line["cpu_baseline"] = cpu_baseline(cfg, eps, b_host, args.storage)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

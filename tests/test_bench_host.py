@@ -35,3 +35,21 @@ def test_kernel_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.kernel_source_digest(["k.cu"]) == d0
     (tmp_path / "k.cu").write_text("int f(int a) {\n  return a + 2;\n}\n")
     assert bench.kernel_source_digest(["k.cu"]) != d0
+
+
+def test_trial_and_backprojection_bytes_follow_the_scope_table():
+    # f-only trial 8 nnz + 12 m + 8 N, 12 B per voxel for the projected step,
+    # 12 more per voxel for UPN's extrapolation; back projection 8 nnz + 4 m + 8 N
+    g = bench.trial_bytes(M, N, NNZ, "fp32", "gpbb")
+    u = bench.trial_bytes(M, N, NNZ, "fp32", "upn")
+    assert round(g / 1e6, 1) == 163.8 and u - g == 12 * N
+    assert round(bench.backprojection_bytes(M, N, NNZ, "fp32") / 1e6, 1) == 158.8
+    assert g - bench.trial_bytes(M, N, NNZ, "bf16", "gpbb") == 2 * NNZ
+
+
+def test_both_arms_print_the_same_config():
+    import synth
+    cfg = synth.get_config("c64")
+    a = bench.bench_config(cfg, 1e-4, NNZ, "fp32", 1, 1)
+    assert a == bench.bench_config(cfg, 1e-4, NNZ, "fp32", True, 1)
+    assert a["m"] == M and a["N"] == N and a["nnz"] == NNZ
