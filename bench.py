@@ -615,21 +615,41 @@ def run_batch(args):
         torch.cuda.synchronize()
         t_batch = (time.perf_counter() - t0) / args.steps
         t0 = time.perf_counter()
+        alone = []  # each problem solved alone, with the whole GPU (the call synchronises)
         for s_, b, x in zip(systems, bs, xs):
+            t1 = time.perf_counter()
             s_.solve("upn", b, alpha, tau, eps, x.zero_())
+            alone.append(time.perf_counter() - t1)
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
         moved = 0.0  # algorithmic bytes of the launches that did work (a trial per f-eval)
+        per_bytes = []
         for s_, r in zip(systems, rb):
             bb, bf = solver_launch_bytes(s_.m, s_.N, s_.nnz, storage, "upn")
-            moved += r.g_evals * bb + r.f_evals * bf
+            per_bytes.append(r.g_evals * bb + r.f_evals * bf)
+            moved += per_bytes[-1]
         peak, _ = measured_peak_gbs()
+        # Lower bound of any schedule of these solves on these kernels: no
+        # problem finishes before it does alone (its passes are a chain), and
+        # the bytes cannot move faster than the best rate any problem reaches
+        # alone.
+        best_rate = max(w / t for w, t in zip(per_bytes, alone))
+        bound = max(max(alone), moved / best_rate)
+        order = sorted(range(len(systems)), key=lambda i: -alone[i])
+        schedule_bound = {
+            "sum_alone_s": sum(alone), "max_alone_s": max(alone),
+            "best_alone_rate_gbs": best_rate / 1e9, "bytes_over_best_rate_s": moved / best_rate,
+            "lower_bound_s": bound, "batch_over_lower_bound": t_batch / bound,
+            "largest_alone": [{"n": systems[i].n,
+                               "m": systems[i].m, "nnz": systems[i].nnz, "alone_s": alone[i],
+                               "gbs_alone": per_bytes[i] / alone[i] / 1e9} for i in order[:6]]}
         res[f"batch48_{storage}"] = {
             "solves_per_s": len(systems) / t_batch, "ms": 1e3 * t_batch,
             "algorithmic_gb": moved / 1e9, "achieved_gbs": moved / t_batch / 1e9,
             "frac_of_measured_hbm": moved / t_batch / 1e9 / peak,
             "one_by_one_solves_per_s": len(systems) / t_seq,
-            "converged": sum(r.status == 0 for r in rb), "iters_total": sum(r.iters for r in rb)}
+            "converged": sum(r.status == 0 for r in rb), "iters_total": sum(r.iters for r in rb),
+            "schedule_bound": schedule_bound}
         del systems, bs, xs
         torch.cuda.empty_cache()
 

@@ -214,6 +214,26 @@ TVR_API int tvr_project_Q(float *x, int64_t n, void *stream);
 TVR_API int tvr_gradient_map_norm(const tvr_system *sys, const float *x, const float *grad, double nu,
                           double *out, void *stream);
 
+/*
+ * The sums behind the acceptance tests of one projected step (Alg. 1, Alg. 2;
+ * the BT and nonmonotone tests of Sec. III-A and III-B), exactly as a solver's
+ * trial computes them: from the base point p with gradient g and the step s,
+ *   xbar = P_Q(p - s g) (float32, rounded as the trial rounds it), d = xbar - p,
+ *   sums[0] = ||A xbar - b||^2     sums[1] = ||A d||^2
+ *   sums[2] = g^T d                sums[3] = ||d||^2
+ *   sums[4] = sum_j B_h(D_j xbar; D_j p)  (Huber Bregman divergence at tau)
+ *   sums[5] = TV_tau(xbar)
+ * accumulated on the device in double-single and finished in FP64, the
+ * precision the line-search decisions rest on.  p, g (N floats), b (m floats)
+ * and the optional outputs xbar (N floats) and resid (m floats, A xbar - b)
+ * are DEVICE memory; sums is a HOST array of 6 doubles (the call
+ * synchronises `stream`).  Uses the system's solver workspace: do not run it
+ * concurrently with a solve on the same system.  s > 0 and tau > 0, finite.
+ */
+TVR_API int tvr_trial_sums(const tvr_system *sys, const float *p, const float *g, const float *b,
+                           double s, double tau, double sums[6], float *xbar, float *resid,
+                           void *stream);
+
 /* Stopping normalisation of the gradient-map test (Sec. III-D). */
 typedef enum tvr_stop_mode {
   TVR_STOP_REL = 0,   /* ||G_k|| / ||G_0|| <= eps (G_0: gradient map of iteration 0) */

@@ -203,6 +203,22 @@ class System:
                                           _stream(stream, x, grad)), "tvr_gradient_map_norm")
         return out.value
 
+    def trial_sums(self, p, g, b, step: float, tau: float, xbar=None, resid=None,
+                   stream=None):
+        """The FP64 sums of one projected trial step from p along g (Alg. 1 and
+        Alg. 2's tests): {||A xbar - b||^2, ||A d||^2, g^T d, ||d||^2,
+        sum_j B_h(D_j xbar; D_j p), TV_tau(xbar)}; device vectors only."""
+        pp, _ = _ptr(p, self.N, "p")
+        pgr, _ = _ptr(g, self.N, "g")
+        pb, _ = _ptr(b, self.m, "b")
+        px = _ptr(xbar, self.N, "xbar")[0] if xbar is not None else None
+        pr = _ptr(resid, self.m, "resid")[0] if resid is not None else None
+        out = (ctypes.c_double * 6)()
+        check(lib().tvr_trial_sums(self._h, pp, pgr, pb, float(step), float(tau),
+                                   ctypes.cast(out, ctypes.c_void_p), px, pr,
+                                   _stream(stream, p, g, b)), "tvr_trial_sums")
+        return list(out)
+
     # ---- solvers ----
     def solve(self, method: str, b, alpha: float, tau: float, eps: float, x,
               opts: SolveOptions | None = None, stream=None,

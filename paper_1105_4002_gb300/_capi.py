@@ -72,6 +72,7 @@ SIGNATURES = {
     "tvr_phi_vjp_f64": (ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "tvr_project_Q": (ctypes.c_int, [_P, _I64, _P]),
     "tvr_gradient_map_norm": (ctypes.c_int, [_P, _P, _P, _D, _P, _P]),
+    "tvr_trial_sums": (ctypes.c_int, [_P, _P, _P, _P, _D, _D, _P, _P, _P, _P]),
     "tvr_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "tvr_solve_gp": (ctypes.c_int, [_P, _P, _D, _D, _D, ctypes.POINTER(SolveOpts), _P,
                                     ctypes.POINTER(SolveInfo), _P]),

@@ -865,3 +865,8 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
   launch_pdl(trial, grid, s, A, nullptr, nullptr, nullptr, ws.fwd, st, slot(0), nullptr);
   mark(0, 1);
 }
+
+void launch_trial(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
+  launch_pdl(fwd_kernel<FWD_TRIAL>(A), ws.grid_trial, s, A, nullptr, nullptr, nullptr, ws.fwd, st,
+             -1, nullptr);
+}

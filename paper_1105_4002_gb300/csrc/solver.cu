@@ -420,4 +420,66 @@ int tvr_solve_batch(tvr_system *const *systems, int32_t count, int32_t method,
   return worst;
 }
 
+int tvr_trial_sums(const tvr_system *csys, const float *p, const float *g, const float *b, double s,
+                   double tau, double sums[6], float *xbar, float *resid, void *stream) {
+  tvr_system *sys = const_cast<tvr_system *>(csys);
+  if (!sys || !p || !g || !b || !sums) return fail(TVR_ERR_ARG, "tvr_trial_sums: null argument");
+  if (!finite_pos(s) || !finite_pos(tau))
+    return fail(TVR_ERR_ARG, "tvr_trial_sums: need s > 0 and tau > 0 (finite)");
+  if (!is_device_ptr(p) || !is_device_ptr(g) || !is_device_ptr(b) ||
+      (xbar && !is_device_ptr(xbar)) || (resid && !is_device_ptr(resid)))
+    return fail(TVR_ERR_ARG, "tvr_trial_sums: vectors must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int rc = ensure_solver(sys, 0)) return rc;
+  // the (p_j, g_j) pairs the trial gathers, interleaved by two strided copies
+  TVR_CUDA(cudaMemcpy2DAsync(sys->pg, sizeof(float2), p, sizeof(float), sizeof(float), sys->N,
+                             cudaMemcpyDeviceToDevice, st));
+  TVR_CUDA(cudaMemcpy2DAsync(reinterpret_cast<float *>(sys->pg) + 1, sizeof(float2), g,
+                             sizeof(float), sizeof(float), sys->N, cudaMemcpyDeviceToDevice, st));
+  // a GP trial at step s (BT's L = 1/s); its control step then accepts or
+  // rejects it in this scratch state, which only moves the roles around
+  DevState h;
+  std::memset(&h, 0, sizeof(h));
+  h.alpha = 0.0;
+  h.tau = tau;
+  h.eps = 0.0;
+  h.rho = 2.0;
+  h.Lbar = 1.0 / s;
+  h.Lt = 1.0 / s;
+  h.L = 1.0 / s;
+  h.step = s;
+  h.kmax = 1 << 30;
+  h.bt_max = 0;
+  h.solver = SOLVER_GP;
+  h.N = sys->N;
+  h.b = b;
+  for (int k = 0; k < RN_COUNT; ++k) h.vN[k] = sys->vN[k];
+  for (int k = 0; k < RM_COUNT; ++k) h.vM[k] = sys->vM[k];
+  h.pg = sys->pg;
+  h.w = sys->wplanes[0];
+  h.wt = sys->wplanes[1];
+  h.wt2 = sys->wplanes[2];
+  TVR_CUDA(cudaMemcpyAsync(sys->st, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  launch_trial(sys->mat(), sys->st, sys->ws, st);
+  TVR_CUDA(cudaGetLastError());
+  DevState f;
+  TVR_CUDA(cudaMemcpyAsync(&f, sys->st, sizeof(f), cudaMemcpyDeviceToHost, st));
+  TVR_CUDA(cudaStreamSynchronize(st));
+  sums[0] = f.r_fwd[0];
+  sums[1] = f.r_fwd[1];
+  for (int k = 0; k < 3; ++k) sums[2 + k] = f.r_step[k];
+  sums[5] = f.r_step[4];
+  // the trial's outputs are where the roles point after its control step
+  // (an accepted trial swaps x with xbar and r with A xbar - b)
+  const bool accepted = f.k == 1;
+  const float *xb = accepted ? f.vN[RN_X] : f.vN[RN_T];
+  const float *rt = accepted ? f.vM[RM_R] : f.vM[RM_RT];
+  if (xbar)
+    TVR_CUDA(cudaMemcpyAsync(xbar, xb, sizeof(float) * sys->N, cudaMemcpyDeviceToDevice, st));
+  if (resid)
+    TVR_CUDA(cudaMemcpyAsync(resid, rt, sizeof(float) * sys->m, cudaMemcpyDeviceToDevice, st));
+  TVR_CUDA(cudaStreamSynchronize(st));
+  return TVR_OK;
+}
+
 }  // extern "C"

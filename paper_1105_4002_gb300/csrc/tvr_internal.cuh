@@ -482,6 +482,8 @@ struct PassTiming {
 };
 void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspace &ws,
                         cudaStream_t s, const PassTiming *timing = nullptr);
+// The single-point trial kernel alone (GP mode), for tvr_trial_sums.
+void launch_trial(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s);
 
 // Construction of A (build_system.cu).  Rows of the CSR and columns of the
 // CSC are padded to multiples of 4 entries (padding: the last real index with

@@ -50,7 +50,7 @@ def test_batch_matches_oracle_and_host_buffers():
     for (g, b, p), x, r in zip(probs, xs, res):
         ref = oracle.solve_upn(p, np.zeros(g.N), 1e-6)
         assert r.ok and ref.status == 0
-        assert rel_l2(x, ref.x) <= 1e-3, (g.n, rel_l2(x, ref.x))
+        assert rel_l2(x, ref.x) <= 1e-4, (g.n, rel_l2(x, ref.x), r.iters, ref.iters)
 
 
 def test_batch_rejects_duplicate_systems():

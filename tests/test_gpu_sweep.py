@@ -140,3 +140,25 @@ def test_autotuned_row_split_is_a_candidate_and_kept(c32):
     assert r2[0].lanes == r1[0].lanes
     with pytest.raises(TVRError):
         s.solve_sweep("upn", b, ALPHAS[:2], prob.tau, cfg.eps, X, SolveOptions(sweep_lanes=3))
+
+
+def test_sweep_gpbb_columns_where_the_minimiser_is_determined(c32):
+    """At alpha = 0.1 and 0.3, tau = 1e-2 and eps = 1e-8 the stopping point
+    pins down the minimiser (the FP64 oracle's GPBB and UPN agree to 2e-5 at
+    alpha = 0.1), so the sweep's GPBB columns meet 1e-4 against the single
+    solves and the oracle although their BB steps see last-bit differences."""
+    torch, s, prob, cfg = c32
+    from paper_1105_4002_gb300 import SolveOptions
+    alphas, tau, eps = [0.1, 0.3], 1e-2, 1e-8
+    X = torch.zeros(len(alphas) * prob.N, device="cuda")
+    b = dev_f32(torch, prob.b)
+    res = s.solve_sweep("gpbb", b, alphas, tau, eps, X, SolveOptions(k_max=100000))
+    Xh = X.cpu().numpy().reshape(len(alphas), prob.N)
+    for c, a in enumerate(alphas):
+        x1 = torch.zeros(prob.N, device="cuda")
+        r1 = s.solve("gpbb", b, a, tau, eps, x1, SolveOptions(k_max=100000))
+        assert res[c].status == r1.status == 0
+        assert rel_l2(Xh[c], x1.cpu().numpy()) <= 1e-4, (a, res[c].iters, r1.iters)
+        p = oracle.Problem(A=prob.A, b=prob.b, n=prob.n, alpha=a, tau=tau)
+        ref = oracle.solve_gpbb(p, np.zeros(prob.N), eps, oracle.Options(k_max=100000))
+        assert ref.status == 0 and rel_l2(Xh[c], ref.x) <= 1e-4, (a, rel_l2(Xh[c], ref.x))
