@@ -1037,6 +1037,21 @@ def main():
     sysm.profile(False)
     phi_ms = p0.elapsed_time(p1) / args.phi_loop
 
+    # ---- cost of a pass whose kernels return at once (after a rejected trial
+    # no gradient is due; after the stop nothing is): UPN solves that stop at
+    # their first iteration (eps = 1e30), in batches of 512 passes (511 of them
+    # do nothing) against batches of 1 ----
+    def noop_probe(batch, reps=20):
+        o = tvr.SolveOptions(use_graph=bool(args.graph), batch=batch)
+        sysm.solve("upn", b, cfg.alpha, cfg.tau, 1e30, xu.zero_(), o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sysm.solve("upn", b, cfg.alpha, cfg.tau, 1e30, xu.zero_(), o)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+    noop_pass_us = 1e6 * (noop_probe(512, 5) - noop_probe(1, 5)) / 511
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -1099,6 +1114,9 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 4 * (m + N), "d2h_bytes_per_step": 2 * 4 * N},
         "gpu_launches": launches,
+        "noop_pass_us": noop_pass_us,
+        "passes_per_step": (passes_gpbb + passes_upn) / args.steps,
+        "iterations_per_step": (sum(it_gpbb) + sum(it_upn)) / args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -462,7 +462,8 @@ cudaError_t transpose(MatStore &A, cudaStream_t s) {
 
 void free_matrix(MatStore &A) {
   void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col,   A.row,
-                  A.val,     A.cval,    A.qval,    A.qcval,   A.rscale, A.mfv};
+                  A.val,     A.cval,    A.qval,    A.qcval,   A.rscale, A.mfv,
+                  A.mfr,     A.mfs};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   A = MatStore{};
@@ -595,9 +596,27 @@ __global__ void k_mf_views(const ViewRec *__restrict__ views, int V, int kind,
   out[v] = o;
 }
 
+// One thread per ray: the constants mf_len reads, from the same mf_pixel_ray
+// the forward projection evaluates per ray, so both directions apply
+// bit-identical entries.
+__global__ void k_mf_rays(const MfView *__restrict__ views, int kind, int Pu, int Pv, int64_t m,
+                          float4 *__restrict__ rays, float4 *__restrict__ starts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t per = (int64_t)Pu * Pv;
+  const int vi = (int)(i / per);
+  const int64_t rem = i - (int64_t)vi * per;
+  const int q = (int)(rem / Pu), p = (int)(rem - (int64_t)q * Pu);
+  MfRay r;
+  mf_pixel_ray(views[vi], kind, Pu, Pv, p, q, r);
+  rays[i] = make_float4(r.inv[0], r.inv[1], r.inv[2], r.dn);
+  if (starts) starts[i] = make_float4(r.s[0], r.s[1], r.s[2], 0.f);
+}
+
 }  // namespace
 
-// Matrix-free storage: only the view constants.  Synchronises `s`.
+// Matrix-free storage: the view constants and the per-ray table (16 bytes a
+// ray, 32 for parallel beam: no matrix).  Synchronises `s`.
 cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int Pv, int kind,
                               int64_t m, int64_t N, MatStore &A, cudaStream_t s) {
   A = MatStore{};
@@ -612,6 +631,11 @@ cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int
   BM_TRY(owned(&A.mfv, V));
   k_mf_views<<<(V + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ViewRec *>(views_dev), V,
                                               kind, A.mfv);
+  BM_TRY(cudaGetLastError());
+  BM_TRY(owned(&A.mfr, m > 0 ? m : 1));
+  if (kind == TVR_PARALLEL) BM_TRY(owned(&A.mfs, m > 0 ? m : 1));
+  if (m > 0)
+    k_mf_rays<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A.mfv, kind, Pu, Pv, m, A.mfr, A.mfs);
   BM_TRY(cudaGetLastError());
   return cudaStreamSynchronize(s);
 }

@@ -46,6 +46,9 @@ namespace {
 #ifndef TVR_BWD_MIN_BLOCKS
 #define TVR_BWD_MIN_BLOCKS 5
 #endif
+#ifndef TVR_MF_MIN_BLOCKS
+#define TVR_MF_MIN_BLOCKS 4
+#endif
 constexpr int kRowLanes = TVR_ROW_LANES;  // lanes per CSR row
 constexpr int kColLanes = TVR_COL_LANES;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
 static_assert(kColLanes >= 4 && kColLanes <= 32 && (kColLanes & (kColLanes - 1)) == 0, "lanes");
@@ -151,7 +154,7 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool BF, bool MF = false>
-__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
                                             : (MODE == FWD_TRIAL || MODE == FWD_TRIAL_X ||
                                                        MODE == FWD_TRIAL_2
                                                    ? TVR_TRIAL_MIN_BLOCKS
@@ -497,7 +500,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3
 // j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool BF, bool MF = false>
-__global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS : TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
                const double *__restrict__ data_in, double *phi_dev, DevState *st,
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? 3 : TVR_BWD_MIN_BLOCKS)
     float s = 0.f;
     if (MF && valid) {
       // matrix-free: the entries of the column from the view geometry (mf.cuh)
-      mf_column<G>(A.mfv, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
+      mf_column<G>(A.mfv, A.mfr, A.mfs, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
                    [&](int64_t i, float v) { s = __fmaf_rn(v, __ldg(r + i), s); });
     }
     // two-stage software pipeline over the lane's 4-entry groups, as in the

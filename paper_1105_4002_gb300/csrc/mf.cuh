@@ -9,7 +9,11 @@
 //   forward  (row i):    walk the slabs of the ray's major axis, take the
 //                        2-4 candidate voxels of each slab, keep len > 0;
 //   adjoint  (column j): for each view, take the pixels inside the bounding
-//                        box of the voxel's projected corners, keep len > 0.
+//                        box of the voxel's projected corners, keep len > 0;
+//                        each pixel's ray constants (1/d, |d|, start) come
+//                        from a per-ray table that mf_pixel_ray filled once,
+//                        instead of three reciprocals and a square root per
+//                        voxel-pixel pair.
 // Both enumerations are conservative (a margin of 1e-3 voxel / pixel), so the
 // two projections apply exactly the same matrix and are exact transposes of
 // each other; they differ from the FP64 Siddon lengths of the stored matrix
@@ -45,6 +49,16 @@ struct MfRay {
 };
 
 __device__ __forceinline__ float mf_half(int n) { return 0.5f * (float)n; }
+
+// Approximate reciprocal (the PTX rcp.approx instruction, relative error about
+// 2^-23), for the conservative pixel boxes of the adjoint only: an error of
+// 1e-7 of a pixel coordinate of at most a few hundred pixels stays far inside
+// the boxes' 1e-3 pixel margin.  No length a_ij uses it.
+__device__ __forceinline__ float mf_rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ void mf_pixel_ray(const MfView &v, int kind, int Pu, int Pv, int p,
                                              int q, MfRay &r) {
@@ -83,8 +97,31 @@ __device__ __forceinline__ float mf_len(const MfRay &r, int ix, int iy, int iz, 
   return tx > te ? __fmul_rn(__fsub_rn(tx, te), r.dn) : 0.f;
 }
 
+// One axis of mf_len: for the voxel coordinate c on an axis with ray start s
+// and 1/d = inv, the pair (min, max) of the parameters where the ray crosses
+// the voxel's two planes (inv != 0), or whether the ray lies inside the slab
+// (inv == 0).  mf_len's result is (min(1, max..) - max(0, min..)) |d| over the
+// three axes; min and max are exact, so taking them axis by axis in any order
+// gives the same float as mf_len.
+__device__ __forceinline__ bool mf_axis(float s, float inv, int c, float half, float &lo_t,
+                                        float &hi_t) {
+  const float lo = __fsub_rn((float)c, half);
+  if (inv != 0.f) {
+    const float t0 = __fmul_rn(__fsub_rn(lo, s), inv);
+    const float t1 = __fmul_rn(__fsub_rn(__fadd_rn(lo, 1.f), s), inv);
+    lo_t = fminf(t0, t1);
+    hi_t = fmaxf(t0, t1);
+    return true;
+  }
+  lo_t = 0.f;
+  hi_t = 1.f;
+  return s > -half && s >= lo && s < __fadd_rn(lo, 1.f);
+}
+
 // Calls use(j, a_ij) for every voxel j with a_ij > 0 in the slabs
-// k = k0 + lane, k0 + lane + G, ... of the ray's major axis.
+// k = k0 + lane, k0 + lane + G, ... of the ray's major axis.  Each length is
+// mf_len's, evaluated factored: the major axis's crossing parameters once per
+// slab, the other two axes' once per candidate cell.
 template <int G, typename Use>
 __device__ __forceinline__ void mf_row(const MfRay &r, int n, int lane, Use &&use) {
   const float half = mf_half(n);
@@ -117,8 +154,8 @@ __device__ __forceinline__ void mf_row(const MfRay &r, int n, int lane, Use &&us
     return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
   };
   const float sA = pick(r.s, 0), dA = pick(r.d, 0), iA = pick(r.inv, 0);
-  const float s1 = pick(r.s, 1), d1 = pick(r.d, 1);
-  const float s2 = pick(r.s, 2), d2 = pick(r.d, 2);
+  const float s1 = pick(r.s, 1), d1 = pick(r.d, 1), i1v = pick(r.inv, 1);
+  const float s2 = pick(r.s, 2), d2 = pick(r.d, 2), i2v = pick(r.inv, 2);
   if (!(tx > te) || iA == 0.f) return;
   // slab range of the major axis covered by [te, tx] (one slab of margin)
   const float ca = __fadd_rn(__fadd_rn(sA, __fmul_rn(te, dA)), half);
@@ -128,11 +165,13 @@ __device__ __forceinline__ void mf_row(const MfRay &r, int n, int lane, Use &&us
   k1 = k1 > n - 1 ? n - 1 : k1;
   constexpr float kMargin = 1e-3f;
   for (int k = k0 + lane; k <= k1; k += G) {
-    // parameters of the slab's two planes, clipped to the volume range
-    const float p0 = __fmul_rn(__fsub_rn(__fsub_rn((float)k, half), sA), iA);
-    const float p1 = __fmul_rn(__fsub_rn(__fsub_rn((float)(k + 1), half), sA), iA);
-    const float ta = fmaxf(te, fminf(p0, p1)), tb = fminf(tx, fmaxf(p0, p1));
+    // parameters of the slab's two planes (mf_len's pair for the major
+    // axis), and the part of them inside the volume range
+    float mA, MA;
+    mf_axis(sA, iA, k, half, mA, MA);
+    const float ta = fmaxf(te, mA), tb = fminf(tx, MA);
     if (!(tb >= ta)) continue;
+    const float eA = fmaxf(0.f, mA), xA = fminf(1.f, MA);
     const float c10 = __fadd_rn(__fadd_rn(s1, __fmul_rn(ta, d1)), half);
     const float c11 = __fadd_rn(__fadd_rn(s1, __fmul_rn(tb, d1)), half);
     const float c20 = __fadd_rn(__fadd_rn(s2, __fmul_rn(ta, d2)), half);
@@ -143,21 +182,35 @@ __device__ __forceinline__ void mf_row(const MfRay &r, int n, int lane, Use &&us
     lo2 = lo2 < 0 ? 0 : lo2;
     hi1 = hi1 > n - 1 ? n - 1 : hi1;
     hi2 = hi2 > n - 1 ? n - 1 : hi2;
-    for (int i2 = lo2; i2 <= hi2; ++i2)
+    for (int i2 = lo2; i2 <= hi2; ++i2) {
+      float m2, M2;
+      if (!mf_axis(s2, i2v, i2, half, m2, M2)) continue;
+      const float e2 = fmaxf(eA, m2), x2 = fminf(xA, M2);
       for (int i1 = lo1; i1 <= hi1; ++i1) {
+        float m1, M1;
+        if (!mf_axis(s1, i1v, i1, half, m1, M1)) continue;
+        const float e = fmaxf(e2, m1), x = fminf(x2, M1);
+        if (!(x > e)) continue;
+        const float len = __fmul_rn(__fsub_rn(x, e), r.dn);  // = mf_len(r, voxel)
+        if (!(len > 0.f)) continue;
         const int ix = ax == 0 ? k : i1;
         const int iy = ax == 1 ? k : (ax == 0 ? i1 : i2);
         const int iz = ax == 2 ? k : i2;
-        const float len = mf_len(r, ix, iy, iz, half);
-        if (len > 0.f) use((int)(ix + n * (iy + n * iz)), len);
+        use((int)(ix + n * (iy + n * iz)), len);
       }
+    }
   }
 }
 
 // Calls use(i, a_ij) for every ray i with a_ij > 0 of the views
 // v = lane, lane + G, ... for voxel (ix, iy, iz).
+// The rays come from the per-ray table (mfr: 1/d and |d|; mfs: the start of a
+// parallel-beam ray, a cone-beam ray starts at the view's source), which holds
+// what mf_pixel_ray gives for each ray.
 template <int G, typename Use>
-__device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int V, int kind, int Pu,
+__device__ __forceinline__ void mf_column(const MfView *__restrict__ views,
+                                          const float4 *__restrict__ mfr,
+                                          const float4 *__restrict__ mfs, int V, int kind, int Pu,
                                           int Pv, int n, int ix, int iy, int iz, int lane,
                                           Use &&use) {
   const float half = mf_half(n);
@@ -207,7 +260,7 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int 
             cd = __fadd_rn(cd, v.nrm[k]);
           }
         ok = ok && cd > 0.f;  // a corner at or behind the source plane: use the whole detector
-        const float s = __fmul_rn(v.dn, __frcp_rn(cd));
+        const float s = __fmul_rn(v.dn, mf_rcp_approx(cd));
         const float a = __fmaf_rn(s, ca_, v.a0), b = __fmaf_rn(s, cb_, v.b0);
         amin = fminf(amin, a);
         amax = fmaxf(amax, a);
@@ -231,17 +284,31 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views, int 
     // the gathers of the group together
     for (int q = q0; q <= q1; ++q)
       for (int p = p0; p <= p1; p += 4) {
+        const int64_t i0 = ((int64_t)vi * Pv + q) * Pu + p;
         float lv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           lv[t] = 0.f;
           if (p + t <= p1) {
+            const float4 rc = __ldg(mfr + i0 + t);
             MfRay r;
-            mf_pixel_ray(v, kind, Pu, Pv, p + t, q, r);
+            r.inv[0] = rc.x;
+            r.inv[1] = rc.y;
+            r.inv[2] = rc.z;
+            r.dn = rc.w;
+            if (kind == TVR_PARALLEL) {
+              const float4 st = __ldg(mfs + i0 + t);
+              r.s[0] = st.x;
+              r.s[1] = st.y;
+              r.s[2] = st.z;
+            } else {
+              r.s[0] = v.src[0];
+              r.s[1] = v.src[1];
+              r.s[2] = v.src[2];
+            }
             lv[t] = mf_len(r, ix, iy, iz, half);
           }
         }
-        const int64_t i0 = ((int64_t)vi * Pv + q) * Pu + p;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (lv[t] > 0.f) use(i0 + t, lv[t]);

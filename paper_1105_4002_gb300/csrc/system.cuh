@@ -86,6 +86,8 @@ struct tvr_system {
     d.rscale = A.rscale;
     d.mf = A.storage == TVR_STORAGE_MATRIX_FREE;
     d.mfv = A.mfv;
+    d.mfr = A.mfr;
+    d.mfs = A.mfs;
     d.V = A.V;
     d.Pu = A.Pu;
     d.Pv = A.Pv;

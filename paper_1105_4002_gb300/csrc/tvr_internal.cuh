@@ -390,6 +390,9 @@ struct MatDev {
   // matrix-free storage: no arrays above; view constants and scan shape
   int mf;
   const MfView *mfv;
+  // per-ray constants of the matrix-free projector (mf.cuh, mf_ray_table):
+  // {1/d_x, 1/d_y, 1/d_z, |d|} per ray, and the ray start for parallel beam
+  const float4 *mfr, *mfs;
   int V, Pu, Pv, kind;
 };
 
@@ -524,6 +527,7 @@ struct MatStore {
   __nv_bfloat16 *qval = nullptr, *qcval = nullptr;  // BF16 codes (null for FP32)
   float *rscale = nullptr;                          // BF16 per-row scales [m]
   MfView *mfv = nullptr;                            // matrix-free view constants [V]
+  float4 *mfr = nullptr, *mfs = nullptr;            // matrix-free ray table [m] (mfs: parallel)
   int V = 0, Pu = 0, Pv = 0, kind = 0;
 };
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,
