@@ -80,14 +80,17 @@ def parse():
                          "0: launch every pass directly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phi-loop", type=int, default=200)
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"],
-                    help="values of A: float32, or bfloat16 codes with per-row float32 scale")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "mf"],
+                    help="A as float32, as bfloat16 codes with per-row float32 scale, or "
+                         "matrix-free (entries computed on the fly)")
     ap.add_argument("--pattern", default="solve",
-                    choices=["solve", "autograd", "batch", "paper", "grid", "precision", "sweep"],
+                    choices=["solve", "autograd", "batch", "paper", "grid", "precision", "sweep",
+                             "projectors"],
                     help="autograd: phi forward + backward through torch.autograd at 128^3; "
                          "grid: GP, GPBB and UPN over alpha x tau x eps at 64^3; "
                          "precision: GPBB and UPN at 256^3 with A stored three ways; "
-                         "sweep: one 8-alpha sweep at 128^3 (--sweep-kmax iterations)")
+                         "sweep: one 8-alpha sweep at 128^3 (--sweep-kmax iterations); "
+                         "projectors: forward and adjoint projection times of --storage at --config")
     ap.add_argument("--sweep-kmax", type=int, default=20000,
                     help="iteration cap of the sweep pattern (a short run for profiling)")
     ap.add_argument("--roofline-steps", type=int, default=3,
@@ -854,6 +857,57 @@ def run_sweep(args):
         "lanes_rows_cols": list(rs[0].lanes)}), flush=True)
 
 
+def run_projectors(args):
+    """Forward projection y = A x and adjoint z = A^T r alone (tvr_forward,
+    tvr_adjoint) for the storage of --storage on the scan of --config, each
+    timed with CUDA events over --steps launches after --warmup; FP32 storage
+    is timed beside it for comparison."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4002_gb300 as tvr
+    cfg = synth.get_config(args.config)
+    geom = cfg.geometry()
+    out = {}
+    for storage in dict.fromkeys([args.storage, "fp32"]):
+        s = tvr.System(geom, storage=storage)
+        x = torch.tensor(np.random.default_rng(1).uniform(0, 1, s.N), dtype=torch.float32,
+                         device="cuda")
+        r = torch.tensor(np.random.default_rng(2).standard_normal(s.m), dtype=torch.float32,
+                         device="cuda")
+        y = torch.empty(s.m, device="cuda")
+        z = torch.empty(s.N, device="cuda")
+
+        def timed(fn):
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return 1e3 * e0.elapsed_time(e1) / args.steps
+
+        fwd = timed(lambda: s.forward(x, y))
+        adj = timed(lambda: s.adjoint(r, z))
+        out[storage] = {"forward_us": fwd, "adjoint_us": adj, "rays_per_s": s.m / (fwd / 1e6),
+                        "voxel_views_per_s": s.N * cfg.views / (adj / 1e6)}
+        del s
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": f"forward and adjoint projection time, {args.storage} storage",
+        "value": out[args.storage]["forward_us"] + out[args.storage]["adjoint_us"],
+        "unit": "us (forward + adjoint)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": workload(cfg, cfg.eps), "storage": args.storage},
+        "results": out}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -894,6 +948,10 @@ def main():
     if args.pattern == "sweep":
         if rank == 0:
             run_sweep(args)
+        return
+    if args.pattern == "projectors":
+        if rank == 0:
+            run_projectors(args)
         return
 
     import numpy as np
@@ -1071,7 +1129,7 @@ def main():
     roof = None
     nf, msf = prof["forward"]
     nb, msb = prof["backward"]
-    if nf:
+    if nf and args.storage != "mf":  # matrix-free: ALU-bound, no matrix bytes to count
         avg_s = msf / nf / 1e3
         ach = bytes_fwd / avg_s / 1e9
         bk = {k: 1e3 * v[1] / v[0] for k, v in breakdown.items() if v[0]}

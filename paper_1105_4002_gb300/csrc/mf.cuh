@@ -280,6 +280,19 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views,
       p1 = p1 > Pu - 1 ? Pu - 1 : p1;
       q1 = q1 > Pv - 1 ? Pv - 1 : q1;
     }
+    // Cone beam: every ray of the view starts at its source, so mf_len's
+    // differences lo - s and (lo + 1) - s per axis are the same for all of
+    // this voxel's pixels; formed once here, with the same operations, they
+    // give the same floats as mf_len.
+    float dlo[3], dhi[3];
+    bool inside[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float lo = X0[k];
+      dlo[k] = __fsub_rn(lo, v.src[k]);
+      dhi[k] = __fsub_rn(__fadd_rn(lo, 1.f), v.src[k]);
+      inside[k] = v.src[k] > -half && v.src[k] >= lo && v.src[k] < __fadd_rn(lo, 1.f);
+    }
     // pixels in groups of 4 along a detector row: the entries first, then
     // the gathers of the group together
     for (int q = q0; q <= q1; ++q)
@@ -291,22 +304,33 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views,
           lv[t] = 0.f;
           if (p + t <= p1) {
             const float4 rc = __ldg(mfr + i0 + t);
-            MfRay r;
-            r.inv[0] = rc.x;
-            r.inv[1] = rc.y;
-            r.inv[2] = rc.z;
-            r.dn = rc.w;
             if (kind == TVR_PARALLEL) {
+              MfRay r;
+              r.inv[0] = rc.x;
+              r.inv[1] = rc.y;
+              r.inv[2] = rc.z;
+              r.dn = rc.w;
               const float4 st = __ldg(mfs + i0 + t);
               r.s[0] = st.x;
               r.s[1] = st.y;
               r.s[2] = st.z;
+              lv[t] = mf_len(r, ix, iy, iz, half);
             } else {
-              r.s[0] = v.src[0];
-              r.s[1] = v.src[1];
-              r.s[2] = v.src[2];
+              const float inv[3] = {rc.x, rc.y, rc.z};
+              float te = 0.f, tx = 1.f;
+              bool hit = true;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                if (inv[k] != 0.f) {
+                  const float t0 = __fmul_rn(dlo[k], inv[k]), t1 = __fmul_rn(dhi[k], inv[k]);
+                  te = fmaxf(te, fminf(t0, t1));
+                  tx = fminf(tx, fmaxf(t0, t1));
+                } else {
+                  hit = hit && inside[k];
+                }
+              }
+              lv[t] = hit && tx > te ? __fmul_rn(__fsub_rn(tx, te), rc.w) : 0.f;  // = mf_len
             }
-            lv[t] = mf_len(r, ix, iy, iz, half);
           }
         }
 #pragma unroll
