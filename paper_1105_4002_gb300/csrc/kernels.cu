@@ -49,10 +49,22 @@ namespace {
 #ifndef TVR_MF_MIN_BLOCKS
 #define TVR_MF_MIN_BLOCKS 4
 #endif
+#ifndef TVR_MF_ROW_LANES
+#define TVR_MF_ROW_LANES 4
+#endif
+#ifndef TVR_MF_COL_LANES
+#define TVR_MF_COL_LANES 4
+#endif
 constexpr int kRowLanes = TVR_ROW_LANES;  // lanes per CSR row
 constexpr int kColLanes = TVR_COL_LANES;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
+constexpr int kMfRowLanes = TVR_MF_ROW_LANES;  // matrix-free: lanes per ray (slabs split among them)
+constexpr int kMfColLanes = TVR_MF_COL_LANES;  // matrix-free: lanes per voxel (views split among them)
 static_assert(kColLanes >= 4 && kColLanes <= 32 && (kColLanes & (kColLanes - 1)) == 0, "lanes");
 static_assert(kRowLanes >= 1 && kRowLanes <= 32 && (kRowLanes & (kRowLanes - 1)) == 0, "lanes");
+static_assert(kMfColLanes >= 4 && kMfColLanes <= 32 && (kMfColLanes & (kMfColLanes - 1)) == 0,
+              "lanes");
+static_assert(kMfRowLanes >= 1 && kMfRowLanes <= 32 && (kMfRowLanes & (kMfRowLanes - 1)) == 0,
+              "lanes");
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v) {
@@ -756,12 +768,12 @@ void launch_pdl(void (*kernel)(P...), int grid, cudaStream_t s, A &&...args) {
 // Kernel instance for the system's storage (float32 or bfloat16 values).
 template <int MODE>
 auto fwd_kernel(const MatDev &A) {
-  return A.mf ? k_forward<kRowLanes, MODE, false, true>
+  return A.mf ? k_forward<kMfRowLanes, MODE, false, true>
               : (A.bf16 ? k_forward<kRowLanes, MODE, true> : k_forward<kRowLanes, MODE, false>);
 }
 template <int MODE>
 auto bwd_kernel(const MatDev &A) {
-  return A.mf ? k_backward<kColLanes, MODE, false, true>
+  return A.mf ? k_backward<kMfColLanes, MODE, false, true>
               : (A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>);
 }
 
@@ -777,8 +789,9 @@ void kernel_grids(Workspace &ws, const MatDev &A, int device) {
     return (int)(need < grid ? need : grid);
   };
   auto occ = [&](const void *k) { return occupancy_grid(k, TVR_BLOCK, device); };
-  const int64_t rows = (A.m + TVR_BLOCK / kRowLanes - 1) / (TVR_BLOCK / kRowLanes);
-  const int64_t cols = (A.N + TVR_BLOCK / kColLanes - 1) / (TVR_BLOCK / kColLanes);
+  const int rl = A.mf ? kMfRowLanes : kRowLanes, cl = A.mf ? kMfColLanes : kColLanes;
+  const int64_t rows = (A.m + TVR_BLOCK / rl - 1) / (TVR_BLOCK / rl);
+  const int64_t cols = (A.N + TVR_BLOCK / cl - 1) / (TVR_BLOCK / cl);
   const int64_t vox = (A.N + TVR_BLOCK - 1) / TVR_BLOCK;
   const int64_t fwd_need = rows > vox ? rows : vox;
   ws.grid_fwd = cap(occ((const void *)fwd_kernel<FWD_RESID>(A)), rows);
