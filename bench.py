@@ -79,6 +79,9 @@ def parse():
                     help="1: replay passes as CUDA graphs (kernel timing by event nodes); "
                          "0: launch every pass directly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the short runs of the autograd (128^3) and batch (48 problems) "
+                         "configurations that the default line reports under other_configs")
     ap.add_argument("--phi-loop", type=int, default=200)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "mf"],
                     help="A as float32, as bfloat16 codes with per-row float32 scale, or "
@@ -342,8 +345,9 @@ def cpu_baseline(cfg, eps, b_host, storage):
 
 
 # ------------------------------------------------------------- autograd
-def run_autograd(args):
-    """phi(x; b) forward + backward (torch.autograd) on the 128^3 / 60-view / 192^2 problem."""
+def run_autograd(args, emit=True):
+    """phi(x; b) forward + backward (torch.autograd) on the 128^3 / 60-view / 192^2 problem;
+    returns the record (and prints it with emit)."""
     import numpy as np
     import torch
     import synth
@@ -398,7 +402,7 @@ def run_autograd(args):
     name, mst, cnt, by = max([("fwd_csr", msf, nf, bytes_f), ("vjp_csc_tv", msb, nb, bytes_b)],
                              key=lambda c: c[1])
     ach = by / (mst / cnt / 1e3) / 1e9
-    print(json.dumps({
+    rec = {
         "metric": "phi forward+backward (autograd) evals/s at 128^3", "value": 1e3 / ms,
         "unit": "fwd+bwd/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -412,7 +416,10 @@ def run_autograd(args):
                      "avg_us": 1e3 * mst / cnt, "peak_source": src,
                      "fwd_us": 1e3 * msf / max(nf, 1), "bwd_us": 1e3 * msb / max(nb, 1)},
         "gpu_launches": 3 * args.steps,
-        "clocks": clocks}), flush=True)
+        "clocks": clocks}
+    if emit:
+        print(json.dumps(rec), flush=True)
+    return rec
 
 
 # ------------------------------------------------------ paper experiment
@@ -582,8 +589,9 @@ def batch_problems(count=48, seed=5):
     return out
 
 
-def run_batch(args):
-    """solves/s to eps: 48 uneven problems batched vs one by one; 8-alpha sweep at 128^3."""
+def run_batch(args, emit=True, storages=("fp32", "bf16"), sweep=True):
+    """solves/s to eps: 48 uneven problems batched vs one by one; 8-alpha sweep at 128^3;
+    returns the record (and prints it with emit)."""
     import numpy as np
     import torch
     import synth
@@ -603,7 +611,7 @@ def run_batch(args):
                             .astype(np.float32), device=dev)
 
     probs = batch_problems()
-    for storage in ("fp32", "bf16"):
+    for storage in storages:
         systems = [tvr.System(g, storage=storage) for g, _, _ in probs]
         bs = [make_b(s_, xt, z, 0.01) for s_, (g, xt, z) in zip(systems, probs)]
         xs = [torch.zeros(s_.N, device=dev) for s_ in systems]
@@ -658,7 +666,7 @@ def run_batch(args):
 
     cfg = synth.get_config("c128")
     alphas = list(np.logspace(-4, -1, 8))
-    for storage in ("fp32", "bf16"):
+    for storage in (storages if sweep else ()):
         sysm = tvr.System(cfg.geometry(), storage=storage)
         b = make_b(sysm, cfg.phantom(), synth.standard_normal(sysm.m, cfg.seed + 1000), cfg.noise)
         X = torch.zeros(8 * sysm.N, device=dev)
@@ -684,7 +692,7 @@ def run_batch(args):
             "single_iters": its}
         del sysm, X
         torch.cuda.empty_cache()
-    print(json.dumps({
+    rec = {
         "metric": "solves/s to eps=1e-4 (UPN): 48 uneven problems batched; 8-alpha sweep at 128^3",
         "value": res["batch48_fp32"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
         "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
@@ -693,7 +701,10 @@ def run_batch(args):
                                "10 ellipsoids, 1% noise; sweep: 128^3 / 60 views / 192^2, "
                                "alphas 1e-4..1e-1 log-spaced", "alpha": alpha, "tau": tau,
                    "eps": eps},
-        "results": res}), flush=True)
+        "results": res}
+    if emit:
+        print(json.dumps(rec), flush=True)
+    return rec
 
 
 def run_grid(args):
@@ -906,6 +917,36 @@ def run_projectors(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": {"workload": workload(cfg, cfg.eps), "storage": args.storage},
         "results": out}), flush=True)
+
+
+def other_configs():
+    """Short runs of two other configurations, after the main line's timing,
+    so that one default run records them too: phi forward + backward through
+    torch.autograd at 128^3 (10 timed steps) and the 48-problem FP32 batch
+    (one batched solve, then every problem alone, with the schedule bound).
+    A failure is recorded in place of the numbers."""
+    import types
+    out = {}
+    try:
+        r = run_autograd(types.SimpleNamespace(steps=10, warmup=3), emit=False)
+        out["autograd_128cubed"] = {
+            "value": r["value"], "unit": r["unit"], "ms_per_step": r["ms_per_step"],
+            "roofline_frac": r["roofline"]["frac"], "roofline_kernel": r["roofline"]["kernel"],
+            "workload": r["config"]["workload"]}
+    except Exception as e:  # noqa: BLE001 -- reported, not raised
+        out["autograd_128cubed"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    try:
+        r = run_batch(types.SimpleNamespace(steps=1), emit=False, storages=("fp32",), sweep=False)
+        b = r["results"]["batch48_fp32"]
+        out["batch48_fp32"] = {
+            "value": b["solves_per_s"], "unit": "solves/s to eps = 1e-4 (UPN)",
+            "one_by_one_solves_per_s": b["one_by_one_solves_per_s"],
+            "converged": b["converged"],
+            "batch_over_schedule_lower_bound": b["schedule_bound"]["batch_over_lower_bound"],
+            "workload": r["config"]["workload"]}
+    except Exception as e:  # noqa: BLE001 -- reported, not raised
+        out["batch48_fp32"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -1177,6 +1218,8 @@ def main():
         "iterations_per_step": (sum(it_gpbb) + sum(it_upn)) / args.steps,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_other_configs:
+        line["other_configs"] = other_configs()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, eps, b_host, args.storage)
     print(json.dumps(line), flush=True)
