@@ -67,6 +67,13 @@ def l2_note(nnz: int) -> str:
 HBM_FALLBACK_GBS = 6800.0
 
 
+def dtype_of(storage: str) -> str:
+    """The arithmetic type of the path with A stored as `storage`."""
+    return {"fp32": "f32", "bf16": "bf16 values, f32 arithmetic",
+            "u16": "u16 fixed-point values, f32 arithmetic",
+            "mf": "f32 (matrix-free entries)"}[storage]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,9 +90,10 @@ def parse():
                     help="skip the short runs of the autograd (128^3) and batch (48 problems) "
                          "configurations that the default line reports under other_configs")
     ap.add_argument("--phi-loop", type=int, default=200)
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "mf"],
-                    help="A as float32, as bfloat16 codes with per-row float32 scale, or "
-                         "matrix-free (entries computed on the fly)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "u16", "mf"],
+                    help="A as float32, as bfloat16 codes with per-row float32 scale, as 16-bit "
+                         "unsigned fixed-point codes with per-row float32 step, or matrix-free "
+                         "(entries computed on the fly)")
     ap.add_argument("--pattern", default="solve",
                     choices=["solve", "autograd", "batch", "paper", "grid", "precision", "sweep",
                              "projectors"],
@@ -589,7 +597,7 @@ def batch_problems(count=48, seed=5):
     return out
 
 
-def run_batch(args, emit=True, storages=("fp32", "bf16"), sweep=True):
+def run_batch(args, emit=True, storages=("fp32", "bf16", "u16"), sweep=True):
     """solves/s to eps: 48 uneven problems batched vs one by one; 8-alpha sweep at 128^3;
     returns the record (and prints it with emit)."""
     import numpy as np
@@ -755,7 +763,7 @@ def run_grid(args):
                   "grid at 64^3", "value": total_evals / (total_ms / 1e3),
         "unit": "grad-phi evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.storage == "fp32" else "bf16 values, f32 arithmetic",
+        "dtype": dtype_of(args.storage),
         "data": "synthetic",
         "config": {"workload": workload(cfg, cfg.eps), "n": cfg.n, "views": cfg.views,
                    "det": cfg.det, "storage": args.storage, "k_max": 20000},
@@ -785,7 +793,7 @@ def run_precision(args):
     ref = {}
     out = {}
     opts = tvr.SolveOptions(k_max=5000)
-    for storage in ("fp32", "bf16", "mf"):
+    for storage in ("fp32", "bf16", "u16", "mf"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sysm = tvr.System(geom, storage=storage)
@@ -1198,7 +1206,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.storage), "data": "synthetic",
         "data_note": DATA_NOTE,
         "config": bench_config(cfg, eps, nnz, args.storage, args.graph, world),
         "time_to_eps": {"gpbb_ms": sorted(t_gpbb)[len(t_gpbb) // 2],

@@ -61,6 +61,12 @@ typedef enum tvr_storage {
                                    bfloat16 codes q_ij = bf16(a_ij / s_i) (round to nearest even),
                                    the same codes in CSR and CSC; FP32 accumulation; the back
                                    projection applies exactly the transpose of the forward matrix */
+  TVR_STORAGE_U16_ROWSCALE = 3,  /* values a_ij = t_i q_ij: per-row FP32 step t_i = fl(s_i / 65535)
+                                   with s_i = max_j a_ij, and 16-bit unsigned fixed-point codes
+                                   q_ij = min(65535, rint(a_ij / t_i)), the same codes in CSR and
+                                   CSC; 2 bytes per entry like BF16 storage, but each entry within
+                                   half a step (s_i / 131070) of a_ij instead of 2^-9 of it; FP32
+                                   accumulation; exact transpose as for BF16 */
   TVR_STORAGE_MATRIX_FREE = 2   /* no stored A: every projection computes its entries on the fly as
                                    the float32 length of the ray segment (source to pixel centre)
                                    inside the voxel's unit box, from float32 view constants; the
@@ -186,8 +192,8 @@ TVR_API int tvr_phi_vjp_f64(const tvr_system *sys, const double *x, const double
  * the library, about 17.5 MiB (16 MiB residual, 1.5 MiB reductions), held on
  * every GPU that loads the library until the process exits, so:
  *   - the system's rays m must be <= 4,194,304, else TVR_ERR_ARG;
- *   - the system must store A as FP32 CSR or be matrix-free; BF16 row-scale
- *     storage needs a second, row-scaled residual and is refused (TVR_ERR_ARG);
+ *   - the system must store A as FP32 CSR or be matrix-free; BF16 and U16
+ *     row-scale storage need a second, row-scaled residual and are refused (TVR_ERR_ARG);
  *   - x, b (and grad, phi_dev when given) must be DEVICE memory (host data
  *     would need staging buffers), else TVR_ERR_ARG;
  *   - the first call on a device looks up the array's device address (once

@@ -107,7 +107,7 @@ class System:
     """A built system matrix (owns A and all device workspace)."""
 
     STORAGE = {"fp32": _capi.TVR_STORAGE_FP32, "bf16": _capi.TVR_STORAGE_BF16_ROWSCALE,
-               "mf": _capi.TVR_STORAGE_MATRIX_FREE}
+               "u16": _capi.TVR_STORAGE_U16_ROWSCALE, "mf": _capi.TVR_STORAGE_MATRIX_FREE}
 
     def __init__(self, geometry, stream=None, storage: str = "fp32"):
         views = np.ascontiguousarray(geometry.views, dtype=np.float64)

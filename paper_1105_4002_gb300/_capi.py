@@ -21,6 +21,7 @@ TVR_PARALLEL = 1
 TVR_STORAGE_FP32 = 0
 TVR_STORAGE_BF16_ROWSCALE = 1
 TVR_STORAGE_MATRIX_FREE = 2
+TVR_STORAGE_U16_ROWSCALE = 3
 TVR_STOP_REL = 0
 TVR_STOP_PER_N = 1
 TVR_VIEW_FIELDS = 12

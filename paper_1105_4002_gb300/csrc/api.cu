@@ -113,7 +113,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   if (!g || !out) return fail(TVR_ERR_ARG, "tvr_build_system: null argument");
   *out = nullptr;
   if (storage != TVR_STORAGE_FP32 && storage != TVR_STORAGE_BF16_ROWSCALE &&
-      storage != TVR_STORAGE_MATRIX_FREE)
+      storage != TVR_STORAGE_U16_ROWSCALE && storage != TVR_STORAGE_MATRIX_FREE)
     return fail(TVR_ERR_ARG, "tvr_build_system: unknown storage");
   if (g->n < 1 || g->n_views < 1 || g->det_cols < 1 || g->det_rows < 1 || !g->views ||
       (g->kind != TVR_CONE && g->kind != TVR_PARALLEL) || g->reserved != 0)
@@ -158,6 +158,7 @@ int tvr_build_system(const tvr_geometry *g, int32_t storage, void *stream, tvr_s
   } else {
     BUILD_CUDA(build_matrix(views_dev, g->n, g->det_cols, g->det_rows, g->kind, m, N, sys->A, s));
     if (storage == TVR_STORAGE_BF16_ROWSCALE) BUILD_CUDA(quantize_bf16(sys->A, s));
+    if (storage == TVR_STORAGE_U16_ROWSCALE) BUILD_CUDA(quantize_u16(sys->A, s));
     BUILD_CUDA(interleave_lanes(sys->A, s));
   }
   sys->nnz = sys->A.nnz;
@@ -200,7 +201,7 @@ int tvr_system_export_csr(const tvr_system *sys, int64_t *row_ptr, int32_t *col,
   TVR_CUDA(cudaDeviceSynchronize());
   const float *vd = sys->A.val;
   float *tmp = nullptr;
-  if (val && sys->A.storage == TVR_STORAGE_BF16_ROWSCALE) {
+  if (val && coded16(sys->A.storage)) {
     TVR_CUDA(cudaMalloc(&tmp, sizeof(float) * (sys->A.nnz_pad > 0 ? sys->A.nnz_pad : 1)));
     cudaError_t e = effective_values(sys->A, false, tmp, 0);
     if (e != cudaSuccess) {
@@ -223,7 +224,7 @@ int tvr_system_export_csc(const tvr_system *sys, int64_t *col_ptr, int32_t *row,
   TVR_CUDA(cudaDeviceSynchronize());
   const float *vd = sys->A.cval;
   float *tmp = nullptr;
-  if (val && sys->A.storage == TVR_STORAGE_BF16_ROWSCALE) {
+  if (val && coded16(sys->A.storage)) {
     TVR_CUDA(cudaMalloc(&tmp, sizeof(float) * (sys->A.nnz_cpad > 0 ? sys->A.nnz_cpad : 1)));
     cudaError_t e = effective_values(sys->A, true, tmp, 0);
     if (e != cudaSuccess) {

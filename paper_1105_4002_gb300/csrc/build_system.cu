@@ -671,13 +671,42 @@ __global__ void k_quantize(const int64_t *__restrict__ ptr, const int32_t *__res
   }
 }
 
-__global__ void k_effective(const int64_t *__restrict__ ptr, const int32_t *__restrict__ rows,
-                            const __nv_bfloat16 *__restrict__ q, const float *__restrict__ sc,
-                            int64_t nseg, float *__restrict__ out) {
+// 16-bit unsigned fixed point: the per-row step t = fl(s / 65535) replaces the
+// row maximum s in sc, then q = min(65535, rint(a / t)) for real entries, 0
+// for padding.  Thread per row (CSR) or per column (CSC, row from `rows`).
+__global__ void k_row_step(float *__restrict__ sc, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) sc[i] = __fdiv_rn(sc[i], 65535.f);
+}
+
+__global__ void k_quantize_u16(const int64_t *__restrict__ ptr, const int32_t *__restrict__ len,
+                               const int32_t *__restrict__ rows, const float *__restrict__ val,
+                               const float *__restrict__ sc, int64_t nseg,
+                               uint16_t *__restrict__ q) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nseg) return;
-  for (int64_t e = ptr[c]; e < ptr[c + 1]; ++e)
-    out[e] = __fmul_rn(sc[rows ? rows[e] : c], __bfloat162float(q[e]));
+  const int64_t o = ptr[c], end = ptr[c + 1];
+  for (int64_t e = o; e < end; ++e) {
+    uint16_t code = 0;
+    if (e - o < len[c]) {
+      const unsigned u = __float2uint_rn(__fdiv_rn(val[e], sc[rows ? rows[e] : c]));
+      code = (uint16_t)(u < 65535u ? u : 65535u);
+    }
+    q[e] = code;
+  }
+}
+
+// Effective float32 values t_i * code of 16-bit codes (decode16's formats).
+__global__ void k_effective(const int64_t *__restrict__ ptr, const int32_t *__restrict__ rows,
+                            const __nv_bfloat16 *__restrict__ q, const float *__restrict__ sc,
+                            int64_t nseg, int u16, float *__restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nseg) return;
+  const uint16_t *q16 = reinterpret_cast<const uint16_t *>(q);
+  for (int64_t e = ptr[c]; e < ptr[c + 1]; ++e) {
+    const float code = u16 ? __uint2float_rn(q16[e]) : __bfloat162float(q[e]);
+    out[e] = __fmul_rn(sc[rows ? rows[e] : c], code);
+  }
 }
 
 }  // namespace
@@ -699,6 +728,28 @@ cudaError_t quantize_bf16(MatStore &A, cudaStream_t s) {
   cudaFree(A.cval);
   A.val = A.cval = nullptr;
   A.storage = TVR_STORAGE_BF16_ROWSCALE;
+  return cudaSuccess;
+}
+
+// Replace the FP32 values by per-row steps and 16-bit unsigned fixed-point
+// codes (CSR and CSC get the same code for the same entry: the same quotient,
+// rounded once).
+cudaError_t quantize_u16(MatStore &A, cudaStream_t s) {
+  BM_TRY(owned(&A.rscale, A.m));
+  BM_TRY(owned(&A.qval, A.nnz_pad));
+  BM_TRY(owned(&A.qcval, A.nnz_cpad));
+  k_row_scale<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, A.row_len, A.val, A.m, A.rscale);
+  k_row_step<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.rscale, A.m);
+  k_quantize_u16<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(
+      A.row_ptr, A.row_len, nullptr, A.val, A.rscale, A.m, reinterpret_cast<uint16_t *>(A.qval));
+  k_quantize_u16<<<blocks_for(A.N), TVR_BLOCK, 0, s>>>(
+      A.col_ptr, A.col_len, A.row, A.cval, A.rscale, A.N, reinterpret_cast<uint16_t *>(A.qcval));
+  BM_TRY(cudaGetLastError());
+  BM_TRY(cudaStreamSynchronize(s));
+  cudaFree(A.val);
+  cudaFree(A.cval);
+  A.val = A.cval = nullptr;
+  A.storage = TVR_STORAGE_U16_ROWSCALE;
   return cudaSuccess;
 }
 
@@ -748,9 +799,11 @@ cudaError_t interleave_lanes(MatStore &A, cudaStream_t s) {
 // FP32 values the kernels apply, in stored (padded) order: CSR or CSC.
 cudaError_t effective_values(const MatStore &A, bool csc, float *out, cudaStream_t s) {
   if (csc)
-    k_effective<<<blocks_for(A.N), TVR_BLOCK, 0, s>>>(A.col_ptr, A.row, A.qcval, A.rscale, A.N, out);
+    k_effective<<<blocks_for(A.N), TVR_BLOCK, 0, s>>>(A.col_ptr, A.row, A.qcval, A.rscale, A.N,
+                                                      A.storage == TVR_STORAGE_U16_ROWSCALE, out);
   else
-    k_effective<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, nullptr, A.qval, A.rscale, A.m, out);
+    k_effective<<<blocks_for(A.m), TVR_BLOCK, 0, s>>>(A.row_ptr, nullptr, A.qval, A.rscale, A.m,
+                                                      A.storage == TVR_STORAGE_U16_ROWSCALE, out);
   BM_TRY(cudaGetLastError());
   return cudaStreamSynchronize(s);
 }

@@ -75,16 +75,12 @@ __device__ __forceinline__ float group_sum(float v) {
 
 __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 
-// Four stored values at a 4-aligned position: float32, or bfloat16 codes
-// widened to float32 (a bfloat16 is the upper half of a float32's bits).
-template <bool BF>
+// Four stored values at a 4-aligned position: float32, or 16-bit codes
+// widened to float32 (decode16: bfloat16, or unsigned fixed point with U16).
+template <bool BF, bool U16>
 __device__ __forceinline__ float4 load4(const float *__restrict__ v32,
                                         const __nv_bfloat16 *__restrict__ v16, int64_t e) {
-  if (BF) {
-    const uint2 raw = ld_stream2(v16 + e);
-    return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
-                       __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
-  }
+  if (BF) return decode16<U16>(ld_stream2(v16 + e));
   return ld_stream(v32 + e);
 }
 
@@ -165,7 +161,7 @@ enum BwdMode { BWD_GRAD = 0, BWD_ADJ = 1, BWD_INIT = 2, BWD_SOLVER = 3, BWD_VJP 
 // Forward projection.  G lanes per row, rows of a warp are consecutive (rays
 // of neighbouring detector pixels, which share voxels: x gathers hit in L1).
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool BF, bool MF = false>
+template <int G, int MODE, bool BF, bool MF = false, bool U16 = false>
 __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
                                             : (MODE == FWD_TRIAL || MODE == FWD_TRIAL_X ||
                                                        MODE == FWD_TRIAL_2
@@ -272,7 +268,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
       float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
       if (e0 < end) {
         cn = ld_stream(A.col + e0);
-        vn = load4<BF>(A.val, A.qval, e0);
+        vn = load4<BF, U16>(A.val, A.qval, e0);
       }
       for (; e0 < end; e0 += 4 * G) {
         const int4 c4 = cn;
@@ -284,7 +280,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
           const float2 q2 = __ldg(pg + c4.z), q3 = __ldg(pg + c4.w);
           if (e1 < end) {
             cn = ld_stream(A.col + e1);
-            vn = load4<BF>(A.val, A.qval, e1);
+            vn = load4<BF, U16>(A.val, A.qval, e1);
           }
           const float b0 = xbar_of(q0.x, q0.y, s), b1 = xbar_of(q1.x, q1.y, s);
           const float b2 = xbar_of(q2.x, q2.y, s), b3 = xbar_of(q3.x, q3.y, s);
@@ -313,7 +309,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
           const float x2 = __ldg(x + c4.z), x3 = __ldg(x + c4.w);
           if (e1 < end) {
             cn = ld_stream(A.col + e1);
-            vn = load4<BF>(A.val, A.qval, e1);
+            vn = load4<BF, U16>(A.val, A.qval, e1);
           }
           sx = __fmaf_rn(v4.x, x0, sx);
           sx = __fmaf_rn(v4.y, x1, sx);
@@ -511,7 +507,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
 // lanes 0..3 of a group evaluate the Huber weights of voxels j, j-ex, j-ey,
 // j-ez, whose sum gives [grad TV_tau(x)]_j = -sum_e w_j,e + sum_e w_{j-e},e.
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool BF, bool MF = false>
+template <int G, int MODE, bool BF, bool MF = false, bool U16 = false>
 __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS : TVR_BWD_MIN_BLOCKS)
     k_backward(MatDev A, const float *__restrict__ rin, const float *__restrict__ xin, float alpha,
                float tau, double alpha_d, float *__restrict__ gout, RedSlot slot,
@@ -603,7 +599,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS : TVR_BWD_MI
     float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e0 < end) {
       in4 = ld_stream(A.row + e0);
-      vn = load4<BF>(A.cval, A.qcval, e0);
+      vn = load4<BF, U16>(A.cval, A.qcval, e0);
     }
     for (; e0 < end; e0 += 4 * G) {
       const int4 i4 = in4;
@@ -613,7 +609,7 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS : TVR_BWD_MI
       const int64_t e1 = e0 + 4 * G;
       if (e1 < end) {
         in4 = ld_stream(A.row + e1);
-        vn = load4<BF>(A.cval, A.qcval, e1);
+        vn = load4<BF, U16>(A.cval, A.qcval, e1);
       }
       if (BF && (MODE == BWD_ADJ || MODE == BWD_VJP)) {  // caller's r: apply the row scales
         r0 = __fmul_rn(r0, __ldg(A.rscale + i4.x));
@@ -769,12 +765,16 @@ void launch_pdl(void (*kernel)(P...), int grid, cudaStream_t s, A &&...args) {
 template <int MODE>
 auto fwd_kernel(const MatDev &A) {
   return A.mf ? k_forward<kMfRowLanes, MODE, false, true>
-              : (A.bf16 ? k_forward<kRowLanes, MODE, true> : k_forward<kRowLanes, MODE, false>);
+              : (A.bf16 ? (A.u16 ? k_forward<kRowLanes, MODE, true, false, true>
+                                 : k_forward<kRowLanes, MODE, true>)
+                        : k_forward<kRowLanes, MODE, false>);
 }
 template <int MODE>
 auto bwd_kernel(const MatDev &A) {
   return A.mf ? k_backward<kMfColLanes, MODE, false, true>
-              : (A.bf16 ? k_backward<kColLanes, MODE, true> : k_backward<kColLanes, MODE, false>);
+              : (A.bf16 ? (A.u16 ? k_backward<kColLanes, MODE, true, false, true>
+                                 : k_backward<kColLanes, MODE, true>)
+                        : k_backward<kColLanes, MODE, false>);
 }
 
 // Grids of the hot kernels, each from the occupancy of the instance that runs

@@ -61,12 +61,13 @@ extern "C" int tvr_phi_and_grad_noalloc(const tvr_system *sys, const float *x, c
   if (!sys || !x || !b) return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: null argument");
   if (!(alpha >= 0.0) || !(tau > 0.0) || !std::isfinite(alpha) || !std::isfinite(tau))
     return tvr_fail(TVR_ERR_ARG, "tvr_phi_and_grad_noalloc: need alpha >= 0 and tau > 0");
-  // BF16 row-scale storage gathers a second, row-scaled residual in the back
-  // projection, which the static scratch does not hold
+  // 16-bit coded storage (BF16 or U16 codes with row scales) gathers a second,
+  // row-scaled residual in the back projection, which the static scratch does
+  // not hold
   if (sys->A.storage != TVR_STORAGE_FP32 && sys->A.storage != TVR_STORAGE_MATRIX_FREE)
     return tvr_fail(TVR_ERR_ARG,
-                    "tvr_phi_and_grad_noalloc: needs FP32 or matrix-free storage (BF16 row-scale "
-                    "storage would need a second residual)");
+                    "tvr_phi_and_grad_noalloc: needs FP32 or matrix-free storage (BF16 or U16 "
+                    "row-scale storage would need a second residual)");
   if (sys->m > kNoallocMaxRows)
     return tvr_fail(TVR_ERR_ARG,
                     "tvr_phi_and_grad_noalloc: the system has more rays than the static scratch "

@@ -26,7 +26,7 @@ namespace {
 int ensure_solver(tvr_system *sys, int64_t hist_records) {
   for (auto &p : sys->vN)
     if (int rc = ensure_vec(&p, sys->N)) return rc;
-  const int nm = sys->A.storage == TVR_STORAGE_BF16_ROWSCALE ? RM_COUNT : RM_RS;
+  const int nm = coded16(sys->A.storage) ? RM_COUNT : RM_RS;
   for (int k = 0; k < nm; ++k)
     if (int rc = ensure_vec(&sys->vM[k], sys->m)) return rc;
   if (!sys->pg) TVR_CUDA(cudaMalloc(&sys->pg, sizeof(float2) * (sys->N > 0 ? sys->N : 1)));

@@ -134,7 +134,7 @@ __device__ __forceinline__ float proj(float v) { return v < 0.f ? 0.f : v; }
 // load of indices and one of values, at stride 4 G; any G covers every entry
 // of the lane-interleaved storage exactly once, only the order of additions
 // changes.
-template <int G, bool TWO, bool BF>
+template <int G, bool TWO, bool BF, bool U16 = false>
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_spmm_rows(MatDev A, const float *__restrict__ in0, const float *__restrict__ in1,
                 float *__restrict__ out0, float *__restrict__ out1, const SweepDev *sd, int init) {
@@ -158,9 +158,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       const int4 c4 = ld_stream(A.col + e0);
       float4 v4;
       if (BF) {
-        const uint2 raw = ld_stream2(A.qval + e0);
-        v4 = make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
-                         __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+        v4 = decode16<U16>(ld_stream2(A.qval + e0));
       } else {
         v4 = ld_stream(A.val + e0);
       }
@@ -206,7 +204,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
   }
 }
 
-template <int G, bool BF>
+template <int G, bool BF, bool U16 = false>
 __global__ void __launch_bounds__(TVR_BLOCK)
     k_spmm_cols(MatDev A, const float *__restrict__ in, float *__restrict__ out, const SweepDev *sd,
                 int init) {
@@ -230,9 +228,7 @@ __global__ void __launch_bounds__(TVR_BLOCK)
       const int4 i4 = ld_stream(A.row + e0);
       float4 v4;
       if (BF) {
-        const uint2 raw = ld_stream2(A.qcval + e0);
-        v4 = make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
-                         __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+        v4 = decode16<U16>(ld_stream2(A.qcval + e0));
       } else {
         v4 = ld_stream(A.cval + e0);
       }
@@ -531,15 +527,23 @@ using RowsFn = void (*)(MatDev, const float *, const float *, float *, float *, 
                        int);
 using ColsFn = void (*)(MatDev, const float *, float *, const SweepDev *, int);
 
+// kernel instance for the row split G and the value format (A.bf16: 16-bit
+// codes; A.u16: unsigned fixed point rather than bfloat16)
 template <bool TWO>
-RowsFn rows_fn(int G, bool bf) {
-  if (bf) return G == 2 ? k_spmm_rows<2, TWO, true> : G == 8 ? k_spmm_rows<8, TWO, true>
-                                                              : k_spmm_rows<4, TWO, true>;
+RowsFn rows_fn(int G, const MatDev &A) {
+  if (A.bf16 && A.u16)
+    return G == 2 ? k_spmm_rows<2, TWO, true, true> : G == 8 ? k_spmm_rows<8, TWO, true, true>
+                                                              : k_spmm_rows<4, TWO, true, true>;
+  if (A.bf16) return G == 2 ? k_spmm_rows<2, TWO, true> : G == 8 ? k_spmm_rows<8, TWO, true>
+                                                                   : k_spmm_rows<4, TWO, true>;
   return G == 2 ? k_spmm_rows<2, TWO, false> : G == 8 ? k_spmm_rows<8, TWO, false>
                                                      : k_spmm_rows<4, TWO, false>;
 }
-ColsFn cols_fn(int G, bool bf) {
-  if (bf) return G == 2 ? k_spmm_cols<2, true> : G == 8 ? k_spmm_cols<8, true> : k_spmm_cols<4, true>;
+ColsFn cols_fn(int G, const MatDev &A) {
+  if (A.bf16 && A.u16)
+    return G == 2 ? k_spmm_cols<2, true, true> : G == 8 ? k_spmm_cols<8, true, true>
+                                                        : k_spmm_cols<4, true, true>;
+  if (A.bf16) return G == 2 ? k_spmm_cols<2, true> : G == 8 ? k_spmm_cols<8, true> : k_spmm_cols<4, true>;
   return G == 2 ? k_spmm_cols<2, false> : G == 8 ? k_spmm_cols<8, false> : k_spmm_cols<4, false>;
 }
 
@@ -569,9 +573,9 @@ SweepGrids sweep_grids(const MatDev &A, int device, int lanes_rows, int lanes_co
   SweepGrids g;
   g.lanes_rows = lanes_rows;
   g.lanes_cols = lanes_cols;
-  g.rows_two = rows_fn<true>(lanes_rows, bf);
-  g.rows_one = rows_fn<false>(lanes_rows, bf);
-  g.cols = cols_fn(lanes_cols, bf);
+  g.rows_two = rows_fn<true>(lanes_rows, A);
+  g.rows_one = rows_fn<false>(lanes_rows, A);
+  g.cols = cols_fn(lanes_cols, A);
   g.g_rows_two = proj_grid((const void *)g.rows_two, lanes_rows, A.m, device);
   g.g_rows_one = proj_grid((const void *)g.rows_one, lanes_rows, A.m, device);
   g.g_cols = proj_grid((const void *)g.cols, lanes_cols, A.N, device);
@@ -611,7 +615,7 @@ int sweep_tune(const MatDev &A, int device, const SweepBufs &B, const SweepDev *
                cudaStream_t s, int *lanes_rows, int *lanes_cols) {
   static std::mutex mu;
   static std::map<TuneKey, std::pair<int, int>> cache;
-  const TuneKey key{A.m, A.N, A.nnz, A.bf16 ? 1 : 0, device};
+  const TuneKey key{A.m, A.N, A.nnz, A.bf16 ? (A.u16 ? 2 : 1) : 0, device};
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -654,11 +658,11 @@ int sweep_tune(const MatDev &A, int device, const SweepBufs &B, const SweepDev *
   int rc = TVR_OK;
   for (int i = 0; i < 3 && rc == TVR_OK; ++i) {
     const int L = cand[i];
-    const RowsFn fr = rows_fn<true>(L, A.bf16);
+    const RowsFn fr = rows_fn<true>(L, A);
     const int gr = proj_grid((const void *)fr, L, A.m, device);
     rc = timed([&] { fr<<<gr, TVR_BLOCK, 0, s>>>(A, B.XB, B.DD, B.Z, B.ZD, sd, 1); }, &tr[i]);
     if (rc != TVR_OK) break;
-    const ColsFn fc = cols_fn(L, A.bf16);
+    const ColsFn fc = cols_fn(L, A);
     const int gc = proj_grid((const void *)fc, L, A.N, device);
     rc = timed([&] { fc<<<gc, TVR_BLOCK, 0, s>>>(A, B.RG, B.S, sd, 1); }, &tc[i]);
   }

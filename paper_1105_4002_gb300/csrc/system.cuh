@@ -80,7 +80,8 @@ struct tvr_system {
     d.col_ptr = A.col_ptr;
     d.row = A.row;
     d.cval = A.cval;
-    d.bf16 = A.storage == TVR_STORAGE_BF16_ROWSCALE;
+    d.bf16 = coded16(A.storage);
+    d.u16 = A.storage == TVR_STORAGE_U16_ROWSCALE;
     d.qval = A.qval;
     d.qcval = A.qcval;
     d.rscale = A.rscale;

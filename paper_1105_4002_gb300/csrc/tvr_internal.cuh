@@ -382,8 +382,10 @@ struct MatDev {
   const int64_t *col_ptr;  // CSC [N+1], every column padded to a multiple of 4 entries
   const int32_t *row;      // [stored]
   const float *cval;       // [stored]
-  // BF16 storage: a_ij = rscale[i] * q_ij, the same codes q in CSR and CSC
+  // 16-bit coded storage (BF16 or U16): a_ij = rscale[i] * q_ij, the same
+  // codes q in CSR and CSC; u16 selects the code format (decode16)
   int bf16;
+  int u16;
   const __nv_bfloat16 *qval;   // CSR codes [stored]
   const __nv_bfloat16 *qcval;  // CSC codes [stored]
   const float *rscale;         // [m]
@@ -419,6 +421,20 @@ __device__ __forceinline__ uint2 ld_stream2(const void *p) {
                : "=r"(v.x), "=r"(v.y)
                : "l"(p));
   return v;
+}
+
+// Four stored 16-bit codes (two 32-bit words, the first code in the low half)
+// widened to float32: bfloat16 codes (the upper half of a float32's bits), or
+// 16-bit unsigned fixed-point codes (the integer itself, exact in float32; the
+// row scale carries the step).  The format is a compile-time choice of each
+// kernel instance.
+template <bool U16>
+__device__ __forceinline__ float4 decode16(uint2 raw) {
+  if (U16)
+    return make_float4(__uint2float_rn(raw.x & 0xffffu), __uint2float_rn(raw.x >> 16),
+                       __uint2float_rn(raw.y & 0xffffu), __uint2float_rn(raw.y >> 16));
+  return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                     __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
 }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -536,6 +552,10 @@ int64_t scan_tmp_len(int64_t n);
 cudaError_t build_matrix(const double *views_dev, int n, int Pu, int Pv, int kind, int64_t m,
                          int64_t N, MatStore &A, cudaStream_t s);
 cudaError_t quantize_bf16(MatStore &A, cudaStream_t s);
+cudaError_t quantize_u16(MatStore &A, cudaStream_t s);
+inline bool coded16(int storage) {
+  return storage == TVR_STORAGE_BF16_ROWSCALE || storage == TVR_STORAGE_U16_ROWSCALE;
+}
 cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int Pv, int kind,
                               int64_t m, int64_t N, MatStore &A, cudaStream_t s);
 cudaError_t interleave_lanes(MatStore &A, cudaStream_t s);

@@ -62,3 +62,19 @@ def test_batch_rejects_duplicate_systems():
     with pytest.raises(TVRError):
         solve_batch("upn", [s, s], [bd, bd], [1e-2, 1e-2], 1e-3, 1e-4,
                     [torch.zeros(g.N, device="cuda"), torch.zeros(g.N, device="cuda")])
+
+
+def test_batch_u16_matches_the_unquantised_oracle():
+    """16-bit fixed-point storage (2 bytes per entry, like BF16) keeps the
+    batch's x* within 1e-4 of the FP64 oracle on the unquantised matrix."""
+    torch = cuda()
+    from paper_1105_4002_gb300 import System, solve_batch
+    probs = problems()
+    systems = [System(g, storage="u16") for g, _, _ in probs]
+    bs = [dev_f32(torch, b) for _, b, _ in probs]
+    xs = [torch.zeros(g.N, device="cuda") for g, _, _ in probs]
+    res = solve_batch("upn", systems, bs, [p.alpha for _, _, p in probs], 1e-3, 1e-6, xs)
+    for (g, b, p), x, r in zip(probs, xs, res):
+        ref = oracle.solve_upn(p, np.zeros(g.N), 1e-6)
+        assert r.ok and ref.status == 0
+        assert rel_l2(x.cpu().numpy(), ref.x) <= 1e-4, (g.n, rel_l2(x.cpu().numpy(), ref.x))
