@@ -927,6 +927,54 @@ def run_projectors(args):
         "results": out}), flush=True)
 
 
+def storage_comparison(args, cfg, eps, geom, b, sys_fp32, value_fp32):
+    """The same step (one GPBB and one UPN solve to eps on the same b) with A
+    stored as 16-bit codes, after the FP32 timing: gradient evaluations per
+    second, their ratio to the FP32 value, and the relative L2 distance of each
+    x* from the FP32 solve's."""
+    import numpy as np
+    import torch
+    import paper_1105_4002_gb300 as tvr
+    out = {}
+    ref = {}
+    for m in ("gpbb", "upn"):  # the FP32 solutions, solved again here
+        x = torch.zeros(geom.N, dtype=torch.float32, device=b.device)
+        sys_fp32.solve(m, b, cfg.alpha, cfg.tau, eps, x,
+                       tvr.SolveOptions(use_graph=bool(args.graph)))
+        ref[m] = x.cpu().numpy()
+    for storage in ("bf16", "u16"):
+        try:
+            s16 = tvr.System(geom, storage=storage)
+            xg = torch.zeros(geom.N, dtype=torch.float32, device=b.device)
+            xu = torch.zeros(geom.N, dtype=torch.float32, device=b.device)
+            opts = tvr.SolveOptions(use_graph=bool(args.graph))
+            for _ in range(2):
+                s16.solve("gpbb", b, cfg.alpha, cfg.tau, eps, xg.zero_(), opts)
+                s16.solve("upn", b, cfg.alpha, cfg.tau, eps, xu.zero_(), opts)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            steps = max(min(args.steps, 10), 1)
+            evals = 0
+            e0.record()
+            for _ in range(steps):
+                r1 = s16.solve("gpbb", b, cfg.alpha, cfg.tau, eps, xg.zero_(), opts)
+                r2 = s16.solve("upn", b, cfg.alpha, cfg.tau, eps, xu.zero_(), opts)
+                evals += r1.g_evals + r2.g_evals
+            e1.record()
+            torch.cuda.synchronize()
+            v = evals / (e0.elapsed_time(e1) / 1e3)
+            d = {m: float(np.linalg.norm(x.cpu().numpy() - ref[m]) / np.linalg.norm(ref[m]))
+                 for m, x in (("gpbb", xg), ("upn", xu))}
+            out[storage] = {"value": v, "unit": UNIT, "ratio_to_fp32": v / value_fp32,
+                            "steps": steps, "gpbb_iters": r1.iters, "upn_iters": r2.iters,
+                            "xstar_rel_l2_to_fp32": d, "dtype": dtype_of(storage)}
+            del s16
+        except Exception as e:  # noqa: BLE001 -- reported, not raised
+            out[storage] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
+
+
 def other_configs():
     """Short runs of two other configurations, after the main line's timing,
     so that one default run records them too: phi forward + backward through
@@ -1226,6 +1274,8 @@ def main():
         "iterations_per_step": (sum(it_gpbb) + sum(it_upn)) / args.steps,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_other_configs and args.storage == "fp32":
+        line["vs_plain_fp32"] = storage_comparison(args, cfg, eps, geom, b, sysm, value)
     if world == 1 and not args.no_other_configs:
         line["other_configs"] = other_configs()
     if world == 1 and not args.no_cpu_baseline:
