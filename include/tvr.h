@@ -75,8 +75,15 @@ typedef enum tvr_storage {
                                    footprint) evaluate the same entry function, so they are exact
                                    transposes.  The entries differ from the FP64 Siddon lengths of
                                    the stored kinds by the float32 rounding of the ray geometry.
-                                   Not available: CSR/CSC export, the FP64 and allocation-free
-                                   entry points, tvr_solve_sweep */
+                                   Cone-beam scans whose views all separate into x-y and z parts
+                                   (detector u and normal without z component, w along z, as on a
+                                   circular orbit about z) project by stacks instead, with the
+                                   same entries: the forward walks the x-y path that the rays of
+                                   a detector column share once for 4 of them, the back
+                                   projection the x-y footprint of 4 voxels stacked along z once
+                                   for all 4; such systems hold N + 4 m more floats (the stacks'
+                                   sums).  Not available: CSR/CSC export, the FP64 entry points,
+                                   tvr_solve_sweep */
 } tvr_storage;
 
 /* Number of doubles per view record. */
@@ -194,6 +201,8 @@ TVR_API int tvr_phi_vjp_f64(const tvr_system *sys, const double *x, const double
  *   - the system's rays m must be <= 4,194,304, else TVR_ERR_ARG;
  *   - the system must store A as FP32 CSR or be matrix-free; BF16 and U16
  *     row-scale storage need a second, row-scaled residual and are refused (TVR_ERR_ARG);
+ *     a matrix-free system of separable views also uses its own stack sums,
+ *     allocated when it was built;
  *   - x, b (and grad, phi_dev when given) must be DEVICE memory (host data
  *     would need staging buffers), else TVR_ERR_ARG;
  *   - the first call on a device looks up the array's device address (once

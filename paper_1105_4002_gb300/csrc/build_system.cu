@@ -463,7 +463,7 @@ cudaError_t transpose(MatStore &A, cudaStream_t s) {
 void free_matrix(MatStore &A) {
   void *ptrs[] = {A.row_ptr, A.col_ptr, A.row_len, A.col_len, A.col,   A.row,
                   A.val,     A.cval,    A.qval,    A.qcval,   A.rscale, A.mfv,
-                  A.mfr,     A.mfs};
+                  A.mfr,     A.mfs,     A.mfz,     A.mfy};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   A = MatStore{};
@@ -592,7 +592,10 @@ __global__ void k_mf_views(const ViewRec *__restrict__ views, int V, int kind,
     o.ga[k] = (float)ga[k];
     o.gb[k] = (float)gb[k];
   }
-  for (int k = 0; k < 7; ++k) o.pad[k] = 0.f;
+  // separable view (cleared by k_mf_sep where the ray table disagrees)
+  o.sep = kind != TVR_PARALLEL && o.uu[2] == 0.f && o.nrm[2] == 0.f && o.ww[0] == 0.f &&
+          o.ww[1] == 0.f;
+  for (int k = 0; k < 6; ++k) o.pad[k] = 0.f;
   out[v] = o;
 }
 
@@ -611,6 +614,22 @@ __global__ void k_mf_rays(const MfView *__restrict__ views, int kind, int Pu, in
   mf_pixel_ray(views[vi], kind, Pu, Pv, p, q, r);
   rays[i] = make_float4(r.inv[0], r.inv[1], r.inv[2], r.dn);
   if (starts) starts[i] = make_float4(r.s[0], r.s[1], r.s[2], 0.f);
+}
+
+// One thread per ray of rows q > 0: clears the view's sep flag where the ray's
+// 1/d_x or 1/d_y differs, bit for bit, from that of row 0 of its column.
+__global__ void k_mf_sep(const float4 *__restrict__ rays, int Pu, int Pv, int64_t m,
+                         MfView *__restrict__ views) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t per = (int64_t)Pu * Pv;
+  const int vi = (int)(i / per);
+  const int64_t rem = i - (int64_t)vi * per;
+  const int q = (int)(rem / Pu), p = (int)(rem - (int64_t)q * Pu);
+  if (q == 0) return;
+  const float4 a = rays[i], c = rays[(int64_t)vi * per + p];
+  if (__float_as_int(a.x) != __float_as_int(c.x) || __float_as_int(a.y) != __float_as_int(c.y))
+    atomicAnd(&views[vi].sep, 0);
 }
 
 }  // namespace
@@ -637,7 +656,23 @@ cudaError_t build_matrix_free(const double *views_dev, int n, int V, int Pu, int
   if (m > 0)
     k_mf_rays<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A.mfv, kind, Pu, Pv, m, A.mfr, A.mfs);
   BM_TRY(cudaGetLastError());
-  return cudaStreamSynchronize(s);
+  if (m > 0 && kind != TVR_PARALLEL) {
+    k_mf_sep<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A.mfr, Pu, Pv, m, A.mfv);
+    BM_TRY(cudaGetLastError());
+  }
+  // every view separable: the back projection runs per stack of voxels
+  // (k_mf_adjoint_sep) into a buffer of N values, the forward projection per
+  // stack of rays (k_mf_forward_sep) into one of 4 m row sums
+  std::vector<MfView> hv((size_t)V);
+  BM_TRY(cudaMemcpyAsync(hv.data(), A.mfv, sizeof(MfView) * V, cudaMemcpyDeviceToHost, s));
+  BM_TRY(cudaStreamSynchronize(s));
+  bool sep = m > 0;
+  for (const MfView &v : hv) sep = sep && v.sep;
+  if (sep) {
+    BM_TRY(owned(&A.mfz, N));
+    BM_TRY(owned(&A.mfy, 4 * m));
+  }
+  return cudaSuccess;
 }
 
 // ---- BF16 storage with per-row scale ----

@@ -49,6 +49,21 @@ namespace {
 #ifndef TVR_MF_MIN_BLOCKS
 #define TVR_MF_MIN_BLOCKS 4
 #endif
+#ifndef TVR_MF_SEP_LANES
+#define TVR_MF_SEP_LANES 2
+#endif
+#ifndef TVR_MF_SEP_K
+#define TVR_MF_SEP_K 4
+#endif
+#ifndef TVR_MF_FSEP_LANES
+#define TVR_MF_FSEP_LANES 8
+#endif
+#ifndef TVR_MF_FSEP_K
+#define TVR_MF_FSEP_K 4
+#endif
+#ifndef TVR_MF_SEP_MIN_BLOCKS
+#define TVR_MF_SEP_MIN_BLOCKS 3
+#endif
 #ifndef TVR_MF_ROW_LANES
 #define TVR_MF_ROW_LANES 4
 #endif
@@ -59,6 +74,12 @@ constexpr int kRowLanes = TVR_ROW_LANES;  // lanes per CSR row
 constexpr int kColLanes = TVR_COL_LANES;  // lanes per CSC column (>= 4: TV uses lanes 0..3)
 constexpr int kMfRowLanes = TVR_MF_ROW_LANES;  // matrix-free: lanes per ray (slabs split among them)
 constexpr int kMfColLanes = TVR_MF_COL_LANES;  // matrix-free: lanes per voxel (views split among them)
+constexpr int kMfSepLanes = TVR_MF_SEP_LANES;  // separable matrix-free: lanes per voxel stack
+constexpr int kMfSepK = TVR_MF_SEP_K;          // separable matrix-free: voxels per stack (along z)
+constexpr int kMfFsepLanes = TVR_MF_FSEP_LANES;  // separable matrix-free forward: lanes per ray stack
+constexpr int kMfFsepK = TVR_MF_FSEP_K;          // separable matrix-free forward: rays per stack
+static_assert(kMfSepLanes >= 1 && kMfSepLanes <= 32 && (kMfSepLanes & (kMfSepLanes - 1)) == 0,
+              "lanes");
 static_assert(kColLanes >= 4 && kColLanes <= 32 && (kColLanes & (kColLanes - 1)) == 0, "lanes");
 static_assert(kRowLanes >= 1 && kRowLanes <= 32 && (kRowLanes & (kRowLanes - 1)) == 0, "lanes");
 static_assert(kMfColLanes >= 4 && kMfColLanes <= 32 && (kMfColLanes & (kMfColLanes - 1)) == 0,
@@ -235,7 +256,17 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS
       // extra live register costs more than the latency it hides)
       float bi = 0.f;
       if (!TRIAL && MODE != FWD_Y && valid && lane == 0) bi = __ldg(b + row);
-      if (MF && valid) {
+      if (MF && valid && A.mfy) {
+        // separable views: the row sums from k_mf_forward_sep, launched just before
+        if (lane == 0) {
+          sx = __ldg(A.mfy + row);
+          if (TRIAL) sd = __ldg(A.mfy + A.m + row);
+          if (TWO) {
+            sx2 = __ldg(A.mfy + 2 * A.m + row);
+            sd2 = __ldg(A.mfy + 3 * A.m + row);
+          }
+        }
+      } else if (MF && valid) {
         // matrix-free: the entries of the row from the ray geometry (mf.cuh)
         const int64_t per = (int64_t)A.Pu * A.Pv;
         const int vi = (int)(row / per);
@@ -588,9 +619,14 @@ __global__ void __launch_bounds__(TVR_BLOCK, MF ? TVR_MF_MIN_BLOCKS : TVR_BWD_MI
     }
     float s = 0.f;
     if (MF && valid) {
-      // matrix-free: the entries of the column from the view geometry (mf.cuh)
-      mf_column<G>(A.mfv, A.mfr, A.mfs, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
-                   [&](int64_t i, float v) { s = __fmaf_rn(v, __ldg(r + i), s); });
+      if (A.mfz) {
+        // separable views: (A^T r)_j from k_mf_adjoint_sep, launched just before
+        if (lane == 0) s = __ldg(A.mfz + j);
+      } else {
+        // the entries of the column from the view geometry (mf.cuh)
+        mf_column<G>(A.mfv, A.mfr, A.mfs, A.V, A.kind, A.Pu, A.Pv, A.n, ix, iy, iz, lane,
+                     [&](int64_t i, float v) { s = __fmaf_rn(v, __ldg(r + i), s); });
+      }
     }
     // two-stage software pipeline over the lane's 4-entry groups, as in the
     // forward projection
@@ -724,6 +760,154 @@ __global__ void __launch_bounds__(TVR_BLOCK)
   if (grid_reduce<1>(acc, slot, tot) && threadIdx.x == 0) slot.out[1] = nu * sqrt(tot[0]);
 }
 
+// Matrix-free back projection z = A^T r for scans whose views are all
+// separable (MfView::sep): G lanes per stack of K voxels along z, the views
+// split among the lanes (mf_column_sep), summed over the lanes at the end.
+// The back projection launched next reads z in place of its own pixel
+// enumeration.  With st (solver modes) r is the residual that back projection
+// takes from the device state, and with skip_idle the kernel returns at once
+// where that back projection returns at once.
+template <int G, int K>
+__global__ void __launch_bounds__(TVR_BLOCK, TVR_MF_SEP_MIN_BLOCKS)
+    k_mf_adjoint_sep(MatDev A, const float *__restrict__ rin, DevState *st, int skip_idle,
+                     float *__restrict__ z) {
+  pdl_enter();
+  const float *r = rin;
+  if (st) {
+    if (skip_idle && (st->done || !st->need_grad)) return;
+    r = st->solver == SOLVER_UPN ? st->vM[RM_RY] : st->vM[RM_R];
+  }
+  const int n = A.n;
+  const int64_t stacks = (int64_t)n * n * ((n + K - 1) / K);
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & (G - 1);
+  const int sub = (threadIdx.x & 31) / G;
+  const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
+  const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
+  for (int64_t base = warp * RPW; base < stacks; base += nwarp * RPW) {
+    const int64_t gi = base + sub;
+    const bool valid = gi < stacks;
+    // stack gi = ix + n (iy + n c): x fastest, so a warp's writes of one k
+    // are consecutive voxels (gi < n^3 < 2^31: exact for fast_div)
+    const uint32_t u = valid ? (uint32_t)gi : 0u;
+    const uint32_t c = fast_div(u, A.div_nn);
+    const uint32_t rem = u - c * A.div_nn.d;
+    const uint32_t iy = fast_div(rem, A.div_n);
+    const uint32_t ix = rem - iy * A.div_n.d;
+    const int iz0 = (int)c * K;
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.f;
+    if (valid)
+      for (int vi = lane; vi < A.V; vi += G)
+        mf_column_sep<K>(A.mfv[vi], A.mfr, vi, A.Pu, A.Pv, n, (int)ix, (int)iy, iz0, r, acc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = group_sum<G>(acc[k]);
+    if (valid && lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (iz0 + k < n) z[(int64_t)ix + (int64_t)n * ((int64_t)iy + (int64_t)n * (iz0 + k))] = acc[k];
+    }
+  }
+}
+
+// Matrix-free forward projection for scans whose views are all separable
+// (MfView::sep): G lanes per stack of K rays (rows q of one detector column),
+// the x-y slabs of their shared path split among the lanes (mf_row_sep),
+// summed over the lanes at the end.  The forward projection launched next
+// reads the row sums from y in place of its own walk along each ray:
+//   S = 1: y = A x (x = xin, or with st the point FWD_INIT projects);
+//   S = 2: the trial's A xbar and A d from the pairs (p_j, g_j) and step s;
+//   S = 4: those two and the second trial point's (two-point GPBB pass).
+// y holds S blocks of m values.  The trial modes return at once where the
+// trial kernel does (the solve has stopped).
+template <int G, int K, int S>
+__global__ void __launch_bounds__(TVR_BLOCK, S == 4 ? 3 : TVR_MF_MIN_BLOCKS)  // 4 sums: no spills
+    k_mf_forward_sep(MatDev A, const float *__restrict__ xin, DevState *st,
+                     float *__restrict__ y) {
+  static_assert(S == 1 || S == 2 || S == 4, "sums");
+  pdl_enter();
+  const float *x = xin;
+  const float2 *pg = nullptr;
+  float s = 0.f, sq = 0.f;
+  if (S == 1 && st) x = st->solver == SOLVER_UPN ? st->vN[RN_Y] : st->vN[RN_X];
+  if (S > 1) {
+    if (st->done) return;
+    pg = st->pg;
+    s = (float)st->step;  // the trial kernel's steps, formed the same way
+    if (S == 4) sq = (float)((st->beta * st->beta) * st->theta);
+  }
+  const int64_t per = (int64_t)A.Pu * A.Pv;
+  const int64_t nch = (A.Pv + K - 1) / K;
+  const int64_t stacks = (int64_t)A.V * nch * A.Pu;
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & (G - 1);
+  const int sub = (threadIdx.x & 31) / G;
+  const int64_t warp = ((int64_t)blockIdx.x * TVR_BLOCK + threadIdx.x) >> 5;
+  const int64_t nwarp = (int64_t)gridDim.x * (TVR_BLOCK / 32);
+  for (int64_t base = warp * RPW; base < stacks; base += nwarp * RPW) {
+    const int64_t gi = base + sub;
+    const bool valid = gi < stacks;
+    // stack gi = p + Pu (c + nch vi): p fastest, so a warp's rays are
+    // neighbouring columns
+    const int64_t g = valid ? gi : 0;
+    const int p = (int)(g % A.Pu);
+    const int64_t rest = g / A.Pu;
+    const int c = (int)(rest % nch), vi = (int)(rest / nch);
+    float acc[K][S];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[k][t] = 0.f;
+    if (valid) {
+      const MfView &v = A.mfv[vi];
+      MfRay r0;
+      float izv[K], dzv[K], dnv[K];
+      bool ok[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int q = c * K + k;
+        ok[k] = q < A.Pv;
+        MfRay rk;
+        mf_pixel_ray(v, TVR_CONE, A.Pu, A.Pv, p, ok[k] ? q : 0, rk);
+        if (k == 0) r0 = rk;
+        izv[k] = rk.inv[2];
+        dzv[k] = rk.d[2];
+        dnv[k] = rk.dn;
+      }
+      mf_row_sep<G, K>(r0, izv, dzv, dnv, ok, A.n, lane, [&](int k, int j, float a) {
+        if (S == 1) {
+          acc[k][0] = __fmaf_rn(a, __ldg(x + j), acc[k][0]);
+        } else {
+          const float2 qc = __ldg(pg + j);
+          const float bc = xbar_of(qc.x, qc.y, s);
+          acc[k][0] = __fmaf_rn(a, bc, acc[k][0]);
+          acc[k][1] = __fmaf_rn(a, __fsub_rn(bc, qc.x), acc[k][1]);
+          if (S == 4) {
+            const float bc2 = xbar_of(qc.x, qc.y, sq);
+            acc[k][2] = __fmaf_rn(a, bc2, acc[k][2]);
+            acc[k][3] = __fmaf_rn(a, __fsub_rn(bc2, qc.x), acc[k][3]);
+          }
+        }
+      });
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[k][t] = group_sum<G>(acc[k][t]);
+    if (valid && lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int q = c * K + k;
+        if (q >= A.Pv) continue;
+        const int64_t row = (int64_t)vi * per + (int64_t)q * A.Pu + p;
+#pragma unroll
+        for (int t = 0; t < S; ++t) y[(int64_t)t * A.m + row] = acc[k][t];
+      }
+    }
+  }
+}
+
 int elem_grid(int64_t n, int cap) {
   int64_t b = (n + TVR_BLOCK - 1) / TVR_BLOCK;
   if (b < 1) b = 1;
@@ -800,33 +984,65 @@ void kernel_grids(Workspace &ws, const MatDev &A, int device) {
   ws.grid_trial_2 = cap(occ((const void *)fwd_kernel<FWD_TRIAL_2>(A)), fwd_need);
   ws.grid_bwd = cap(occ((const void *)bwd_kernel<BWD_SOLVER>(A)), cols);
   ws.grid_elem = cap(occ((const void *)k_tv_value), vox);
+  const int64_t stacks = (int64_t)A.n * A.n * ((A.n + kMfSepK - 1) / kMfSepK);
+  ws.grid_mfsep = A.mfz ? cap(occ((const void *)k_mf_adjoint_sep<kMfSepLanes, kMfSepK>),
+                              (stacks + TVR_BLOCK / kMfSepLanes - 1) / (TVR_BLOCK / kMfSepLanes))
+                        : 0;
+  const int64_t rstacks = (int64_t)A.V * ((A.Pv + kMfFsepK - 1) / kMfFsepK) * A.Pu;
+  const int64_t rneed = (rstacks + TVR_BLOCK / kMfFsepLanes - 1) / (TVR_BLOCK / kMfFsepLanes);
+  ws.grid_mfsep_fwd[0] = A.mfy ? cap(occ((const void *)k_mf_forward_sep<kMfFsepLanes, kMfFsepK, 1>), rneed) : 0;
+  ws.grid_mfsep_fwd[1] = A.mfy ? cap(occ((const void *)k_mf_forward_sep<kMfFsepLanes, kMfFsepK, 2>), rneed) : 0;
+  ws.grid_mfsep_fwd[2] = A.mfy ? cap(occ((const void *)k_mf_forward_sep<kMfFsepLanes, kMfFsepK, 4>), rneed) : 0;
+}
+
+// Separable matrix-free scans: the row sums (S of them) into A.mfy ahead of
+// the forward projection that reads them (no launch for other storage).
+template <int S>
+static void launch_mf_fsep(const MatDev &A, const float *x, DevState *st, const Workspace &ws,
+                           cudaStream_t s) {
+  if (!A.mfy) return;
+  launch_pdl(k_mf_forward_sep<kMfFsepLanes, kMfFsepK, S>, ws.grid_mfsep_fwd[S == 1 ? 0 : (S == 2 ? 1 : 2)],
+             s, A, x, st, A.mfy);
+}
+
+// Separable matrix-free scans: A^T r into A.mfz ahead of the back projection
+// that reads it (no launch for other storage).
+static void launch_mf_sep(const MatDev &A, const float *r, DevState *st, int skip_idle,
+                          const Workspace &ws, cudaStream_t s) {
+  if (!A.mfz) return;
+  launch_pdl(k_mf_adjoint_sep<kMfSepLanes, kMfSepK>, ws.grid_mfsep, s, A, r, st, skip_idle, A.mfz);
 }
 
 void launch_forward(const MatDev &A, const float *x, const float *b, float *r, const Workspace &ws,
                     cudaStream_t s, float *rs) {
+  launch_mf_fsep<1>(A, x, nullptr, ws, s);
   launch_pdl(fwd_kernel<FWD_RESID>(A), ws.grid_fwd, s, A, x, b, r, ws.fwd, nullptr, -1, rs);
 }
 
 void launch_forward_plain(const MatDev &A, const float *x, float *y, const Workspace &ws,
                           cudaStream_t s) {
+  launch_mf_fsep<1>(A, x, nullptr, ws, s);
   fwd_kernel<FWD_Y>(A)<<<ws.grid_fwd, TVR_BLOCK, 0, s>>>(A, x, nullptr, y, ws.fwd, nullptr, -1,
                                                           nullptr);
 }
 
 void launch_backward(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                      float *g, const Workspace &ws, double *phi_dev, cudaStream_t s) {
+  launch_mf_sep(A, r, nullptr, 0, ws, s);
   launch_pdl(bwd_kernel<BWD_GRAD>(A), ws.grid_bwd, s, A, r, x, alpha, tau, (double)alpha, g, ws.bwd,
              ws.fwd.out, phi_dev, nullptr, -1, nullptr, nullptr);
 }
 
 void launch_adjoint_plain(const MatDev &A, const float *r, float *z, const Workspace &ws,
                           cudaStream_t s) {
+  launch_mf_sep(A, r, nullptr, 0, ws, s);
   bwd_kernel<BWD_ADJ>(A)<<<ws.grid_bwd, TVR_BLOCK, 0, s>>>(
       A, r, nullptr, 0.f, 1.f, 0.0, z, ws.bwd, nullptr, nullptr, nullptr, -1, nullptr, nullptr);
 }
 
 void launch_vjp(const MatDev &A, const float *r, const float *x, float alpha, float tau,
                 const double *scale, float *gx, float *gb, const Workspace &ws, cudaStream_t s) {
+  launch_mf_sep(A, r, nullptr, 0, ws, s);
   launch_pdl(bwd_kernel<BWD_VJP>(A), ws.grid_bwd, s, A, r, x, alpha, tau, (double)alpha, gx, ws.bwd,
              nullptr, nullptr, nullptr, -1, scale, gb);
 }
@@ -847,8 +1063,10 @@ void launch_gmap_norm(const float *x, const float *g, int64_t n, double nu, cons
 }
 
 void launch_solver_init(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
+  launch_mf_fsep<1>(A, nullptr, st, ws, s);
   launch_pdl(fwd_kernel<FWD_INIT>(A), ws.grid_fwd, s, A, nullptr, nullptr, nullptr, ws.fwd, st, -1,
              nullptr);
+  launch_mf_sep(A, nullptr, st, 0, ws, s);
   launch_pdl(bwd_kernel<BWD_INIT>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
              ws.bwd, nullptr, nullptr, st, -1, nullptr, nullptr);
 }
@@ -867,10 +1085,15 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
   };
   auto slot = [&](int kind) { return tm ? tm->slot[kind] : -1; };
   mark(1, 0);
+  launch_mf_sep(A, nullptr, st, 1, ws, s);
   launch_pdl(bwd_kernel<BWD_SOLVER>(A), ws.grid_bwd, s, A, nullptr, nullptr, 0.f, 1.f, 0.0, nullptr,
              ws.bwd, nullptr, nullptr, st, slot(1), nullptr, nullptr);
   mark(1, 1);
   mark(0, 0);
+  if (solver == PASS_GPBB2)
+    launch_mf_fsep<4>(A, nullptr, st, ws, s);
+  else
+    launch_mf_fsep<2>(A, nullptr, st, ws, s);
   // `solver` is the pass kind: a solver, or PASS_GPBB2 (two trial points)
   auto trial = solver == SOLVER_UPN   ? fwd_kernel<FWD_TRIAL_X>(A)
                : solver == PASS_GPBB2 ? fwd_kernel<FWD_TRIAL_2>(A)
@@ -883,6 +1106,7 @@ void launch_solver_pass(const MatDev &A, DevState *st, int solver, const Workspa
 }
 
 void launch_trial(const MatDev &A, DevState *st, const Workspace &ws, cudaStream_t s) {
+  launch_mf_fsep<2>(A, nullptr, st, ws, s);
   launch_pdl(fwd_kernel<FWD_TRIAL>(A), ws.grid_trial, s, A, nullptr, nullptr, nullptr, ws.fwd, st,
              -1, nullptr);
 }

@@ -27,6 +27,7 @@
 
 #include "tvr_internal.cuh"
 
+
 // Per-view constants (float32).  Pixel (p, q) has centre det + a u + b w with
 // a = p - (Pu - 1)/2, b = q - (Pv - 1)/2; a cone-beam ray starts at src, a
 // parallel-beam ray at src + a u + b w.  nrm is oriented so that dn > 0.
@@ -40,7 +41,13 @@ struct MfView {
   //   parallel: a = ga . X + a0, b = gb . X + b0 (linear)
   float a0, b0;
   float ga[3], gb[3];
-  float pad[7];
+  // cone beam, 1 when the view separates into x-y and z parts: uu, nrm have
+  // no z component and ww only one (so a pixel's column a depends on x, y
+  // alone), and every ray of a detector column p has the same 1/d_x and 1/d_y
+  // floats (checked on the ray table at build time); a circular orbit about z
+  // with the detector rows along z has it.  Else 0.
+  int sep;
+  float pad[6];
 };
 
 struct MfRay {
@@ -337,5 +344,218 @@ __device__ __forceinline__ void mf_column(const MfView *__restrict__ views,
         for (int t = 0; t < 4; ++t)
           if (lv[t] > 0.f) use(i0 + t, lv[t]);
       }
+  }
+}
+
+// Back projection of one separable view (MfView::sep) into K voxels stacked
+// along z at (ix, iy, iz0 .. iz0 + K - 1): acc[k] += sum over the view's rays
+// i of a_ij r_i, j the k-th voxel (voxels at iz >= n are skipped).
+//   Boxes: with uu and nrm free of z, a pixel's column coordinate a and the
+//   depth scale s = dn / ((X - src) . nrm) of a point X depend on its x, y
+//   alone, so the 4 x-y corners of the stack give the columns p0..p1 of all K
+//   voxels; with ww along z, b = b0 + s (z - src_z) ww_z, whose extremes over
+//   voxel k's 8 corners lie at the extreme s and the two z faces, gives its
+//   rows q0_k..q1_k (the same 1e-3 pixel margin as mf_column).
+//   Entries: the rays of a detector column share 1/d_x and 1/d_y, so the x
+//   and y slabs give one parameter interval per column p for all K voxels;
+//   each ray then narrows it by its z slab.  These are mf_len's operations in
+//   its axis order (min and max are exact), so the entries are the same
+//   floats as the forward projection's.  A column whose x-y interval is
+//   already empty holds no entry of these voxels.
+template <int K>
+__device__ __forceinline__ void mf_column_sep(const MfView &v, const float4 *__restrict__ rays,
+                                              int vi, int Pu, int Pv, int n, int ix, int iy,
+                                              int iz0, const float *__restrict__ r,
+                                              float (&acc)[K]) {
+  const float half = mf_half(n);
+  constexpr float kMargin = 1e-3f;
+  const float lim = 1e7f;
+  const float ca = 0.5f * (float)(Pu - 1), cb = 0.5f * (float)(Pv - 1);
+  const float sx = v.src[0], sy = v.src[1], sz = v.src[2];
+  const float xlo = __fsub_rn((float)ix, half), ylo = __fsub_rn((float)iy, half);
+  const float dlx = __fsub_rn(xlo, sx), dhx = __fsub_rn(__fadd_rn(xlo, 1.f), sx);
+  const float dly = __fsub_rn(ylo, sy), dhy = __fsub_rn(__fadd_rn(ylo, 1.f), sy);
+  const bool inx = sx > -half && sx >= xlo && sx < __fadd_rn(xlo, 1.f);
+  const bool iny = sy > -half && sy >= ylo && sy < __fadd_rn(ylo, 1.f);
+  float amin = 3.4e38f, amax = -3.4e38f, smin = 3.4e38f, smax = -3.4e38f;
+  bool ok = true;  // every corner in front of the source plane
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float ex = (c & 1) ? dhx : dlx, ey = (c & 2) ? dhy : dly;
+    const float na = __fmaf_rn(ey, v.uu[1], __fmul_rn(ex, v.uu[0]));
+    const float nd = __fmaf_rn(ey, v.nrm[1], __fmul_rn(ex, v.nrm[0]));
+    ok = ok && nd > 0.f;
+    const float s = __fmul_rn(v.dn, mf_rcp_approx(nd));
+    const float a = __fmaf_rn(s, na, v.a0);
+    amin = fminf(amin, a);
+    amax = fmaxf(amax, a);
+    smin = fminf(smin, s);
+    smax = fmaxf(smax, s);
+  }
+  int p0 = 0, p1 = Pu - 1;  // whole detector unless the box is sound
+  if (ok && fabsf(amin) < lim && fabsf(amax) < lim) {
+    p0 = max(0, (int)ceilf(__fadd_rn(amin, ca) - kMargin));
+    p1 = min(Pu - 1, (int)floorf(__fadd_rn(amax, ca) + kMargin));
+  }
+  int q0[K], q1[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float zlo = __fsub_rn((float)(iz0 + k), half);
+    const float nbl = __fmul_rn(__fsub_rn(zlo, sz), v.ww[2]);
+    const float nbh = __fmul_rn(__fsub_rn(__fadd_rn(zlo, 1.f), sz), v.ww[2]);
+    const float b1 = __fmaf_rn(smin, nbl, v.b0), b2 = __fmaf_rn(smax, nbl, v.b0);
+    const float b3 = __fmaf_rn(smin, nbh, v.b0), b4 = __fmaf_rn(smax, nbh, v.b0);
+    const float bmin = fminf(fminf(b1, b2), fminf(b3, b4));
+    const float bmax = fmaxf(fmaxf(b1, b2), fmaxf(b3, b4));
+    q0[k] = 0;
+    q1[k] = iz0 + k < n ? Pv - 1 : -1;
+    if (ok && fabsf(bmin) < lim && fabsf(bmax) < lim && iz0 + k < n) {
+      q0[k] = max(0, (int)ceilf(__fadd_rn(bmin, cb) - kMargin));
+      q1[k] = min(Pv - 1, (int)floorf(__fadd_rn(bmax, cb) + kMargin));
+    }
+  }
+  const int64_t vbase = (int64_t)vi * Pv * Pu;
+  for (int p = p0; p <= p1; ++p) {
+    // row 0 of column p: its 1/d_x, 1/d_y are every row's
+    const float2 ixy = __ldg(reinterpret_cast<const float2 *>(rays + vbase + p));
+    float te = 0.f, tx = 1.f;
+    bool hit = true;
+    if (ixy.x != 0.f) {
+      const float t0 = __fmul_rn(dlx, ixy.x), t1 = __fmul_rn(dhx, ixy.x);
+      te = fmaxf(te, fminf(t0, t1));
+      tx = fminf(tx, fmaxf(t0, t1));
+    } else {
+      hit = inx;
+    }
+    if (ixy.y != 0.f) {
+      const float t0 = __fmul_rn(dly, ixy.y), t1 = __fmul_rn(dhy, ixy.y);
+      te = fmaxf(te, fminf(t0, t1));
+      tx = fminf(tx, fmaxf(t0, t1));
+    } else {
+      hit = hit && iny;
+    }
+    if (!(hit && tx > te)) continue;
+    // row t of every voxel's row range: the K rays' constants and residuals
+    // loaded together, then used (a residual whose ray misses goes unused)
+    int nt = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nt = max(nt, q1[k] - q0[k] + 1);
+    for (int t = 0; t < nt; ++t) {
+      float2 zw[K];
+      float ri[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        zw[k] = make_float2(0.f, 0.f);
+        ri[k] = 0.f;
+        if (q0[k] + t <= q1[k]) {
+          const int64_t i = vbase + (int64_t)(q0[k] + t) * Pu + p;
+          zw[k] = __ldg(reinterpret_cast<const float2 *>(rays + i) + 1);  // 1/d_z, |d|
+          ri[k] = __ldg(r + i);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (q0[k] + t > q1[k]) continue;
+        const float zlo = __fsub_rn((float)(iz0 + k), half);
+        const float dlz = __fsub_rn(zlo, sz), dhz = __fsub_rn(__fadd_rn(zlo, 1.f), sz);
+        float te2 = te, tx2 = tx;
+        bool h = true;
+        if (zw[k].x != 0.f) {
+          const float t0 = __fmul_rn(dlz, zw[k].x), t1 = __fmul_rn(dhz, zw[k].x);
+          te2 = fmaxf(te2, fminf(t0, t1));
+          tx2 = fminf(tx2, fmaxf(t0, t1));
+        } else {
+          h = sz > -half && sz >= zlo && sz < __fadd_rn(zlo, 1.f);
+        }
+        if (h && tx2 > te2)
+          acc[k] = __fmaf_rn(__fmul_rn(__fsub_rn(tx2, te2), zw[k].y), ri[k], acc[k]);  // = mf_len
+      }
+    }
+  }
+}
+
+// Forward projection of K rays of one detector column of a separable view
+// (MfView::sep): the rays share their start and, bit for bit, their 1/d_x
+// and 1/d_y (and d_x, d_y up to rounding, which only the candidate ranges
+// use), so their paths through the x-y grid are one path.  It is walked once
+// for all K rays: the slabs kA = k0 + lane, k0 + lane + G, ... of the x-y
+// major axis, the 1-3 cells of the other axis in each slab (a 1e-3 voxel
+// margin, as mf_row), and per cell the parameter interval of its x and y
+// slabs; each ray k then takes the z cells its z(t) passes within that
+// interval and narrows it by their z slabs.  These are mf_len's operations
+// (min and max are exact), so every length is the float mf_len gives.
+// r0 is ray 0's geometry (start, d_x, d_y, 1/d_x, 1/d_y); izv, dzv, dnv hold
+// each ray's 1/d_z, d_z and |d|; rays with ok[k] false are skipped.  Calls
+// use(k, j, a_ij) for every voxel j with a_ij > 0 on ray k.
+template <int G, int K, typename Use>
+__device__ __forceinline__ void mf_row_sep(const MfRay &r0, const float (&izv)[K],
+                                           const float (&dzv)[K], const float (&dnv)[K],
+                                           const bool (&ok)[K], int n, int lane, Use &&use) {
+  const float half = mf_half(n);
+  constexpr float kMargin = 1e-3f;
+  // parameter range inside the volume's x-y square (the walk only)
+  float te = 0.f, tx = 1.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    if (r0.inv[a] != 0.f) {
+      const float t0 = __fmul_rn(__fsub_rn(-half, r0.s[a]), r0.inv[a]);
+      const float t1 = __fmul_rn(__fsub_rn(half, r0.s[a]), r0.inv[a]);
+      te = fmaxf(te, fminf(t0, t1));
+      tx = fminf(tx, fmaxf(t0, t1));
+    } else if (!(r0.s[a] > -half && r0.s[a] < half)) {
+      return;
+    }
+  }
+  const int ax = fabsf(r0.d[0]) >= fabsf(r0.d[1]) ? 0 : 1;  // x-y major axis
+  const float sA = ax == 0 ? r0.s[0] : r0.s[1], dA = ax == 0 ? r0.d[0] : r0.d[1];
+  const float iA = ax == 0 ? r0.inv[0] : r0.inv[1];
+  const float sB = ax == 0 ? r0.s[1] : r0.s[0], dB = ax == 0 ? r0.d[1] : r0.d[0];
+  const float iB = ax == 0 ? r0.inv[1] : r0.inv[0];
+  const float sz = r0.s[2];
+  // a separable view's rays all have d . nrm = dn > 0 with nrm in the x-y
+  // plane, so d_x and d_y are never both 0
+  if (!(tx > te) || iA == 0.f) return;
+  const float ca = __fadd_rn(__fadd_rn(sA, __fmul_rn(te, dA)), half);
+  const float cb = __fadd_rn(__fadd_rn(sA, __fmul_rn(tx, dA)), half);
+  int k0 = (int)floorf(fminf(ca, cb)) - 1, k1 = (int)floorf(fmaxf(ca, cb)) + 1;
+  k0 = k0 < 0 ? 0 : k0;
+  k1 = k1 > n - 1 ? n - 1 : k1;
+  for (int kA = k0 + lane; kA <= k1; kA += G) {
+    float mA, MA;
+    mf_axis(sA, iA, kA, half, mA, MA);
+    const float ta = fmaxf(te, mA), tb = fminf(tx, MA);
+    if (!(tb >= ta)) continue;
+    const float eA = fmaxf(0.f, mA), xA = fminf(1.f, MA);
+    const float c0 = __fadd_rn(__fadd_rn(sB, __fmul_rn(ta, dB)), half);
+    const float c1 = __fadd_rn(__fadd_rn(sB, __fmul_rn(tb, dB)), half);
+    int lo = (int)floorf(fminf(c0, c1) - kMargin), hi = (int)floorf(fmaxf(c0, c1) + kMargin);
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > n - 1 ? n - 1 : hi;
+    for (int kB = lo; kB <= hi; ++kB) {
+      float mB, MB;
+      if (!mf_axis(sB, iB, kB, half, mB, MB)) continue;
+      const float e1 = fmaxf(eA, mB), x1 = fminf(xA, MB);
+      if (!(x1 > e1)) continue;
+      const int ix = ax == 0 ? kA : kB, iy = ax == 0 ? kB : kA;
+      const int jxy = ix + n * iy;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (!ok[k]) continue;
+        const float z0 = __fadd_rn(__fadd_rn(sz, __fmul_rn(e1, dzv[k])), half);
+        const float z1 = __fadd_rn(__fadd_rn(sz, __fmul_rn(x1, dzv[k])), half);
+        int lz = (int)floorf(fminf(z0, z1) - kMargin), hz = (int)floorf(fmaxf(z0, z1) + kMargin);
+        lz = lz < 0 ? 0 : lz;
+        hz = hz > n - 1 ? n - 1 : hz;
+        for (int iz = lz; iz <= hz; ++iz) {
+          float mz, Mz;
+          if (!mf_axis(sz, izv[k], iz, half, mz, Mz)) continue;
+          const float e = fmaxf(e1, mz), x = fminf(x1, Mz);
+          if (!(x > e)) continue;
+          const float len = __fmul_rn(__fsub_rn(x, e), dnv[k]);  // = mf_len(ray k, voxel)
+          if (!(len > 0.f)) continue;
+          use(k, jxy + n * n * iz, len);
+        }
+      }
+    }
   }
 }

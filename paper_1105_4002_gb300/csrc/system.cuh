@@ -67,7 +67,7 @@ struct tvr_system {
   int64_t prof_cnt[TVR_PROF_KINDS] = {};
 
   MatDev mat() const {
-    MatDev d;
+    MatDev d{};
     d.n = n;
     d.div_n = make_fastdiv((uint32_t)n);
     d.div_nn = make_fastdiv((uint32_t)n * (uint32_t)n);
@@ -89,6 +89,8 @@ struct tvr_system {
     d.mfv = A.mfv;
     d.mfr = A.mfr;
     d.mfs = A.mfs;
+    d.mfz = A.mfz;
+    d.mfy = A.mfy;
     d.V = A.V;
     d.Pu = A.Pu;
     d.Pv = A.Pv;

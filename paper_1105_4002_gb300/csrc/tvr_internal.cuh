@@ -395,6 +395,12 @@ struct MatDev {
   // per-ray constants of the matrix-free projector (mf.cuh, mf_ray_table):
   // {1/d_x, 1/d_y, 1/d_z, |d|} per ray, and the ray start for parallel beam
   const float4 *mfr, *mfs;
+  // all views separable (MfView::sep): k_mf_adjoint_sep writes A^T r here
+  // and the back projection reads it instead of enumerating pixels; else null
+  float *mfz;
+  // all views separable: k_mf_forward_sep writes up to 4 blocks of m row sums
+  // here and the forward projection reads them instead of walking its rays
+  float *mfy;
   int V, Pu, Pv, kind;
 };
 
@@ -461,6 +467,8 @@ __device__ __forceinline__ void voxel_of(const MatDev &A, int64_t j, int &ix, in
 struct Workspace {
   RedSlot fwd, bwd, step, yf, tv, gmap;
   int grid_fwd, grid_bwd, grid_elem, grid_trial, grid_trial_x, grid_trial_2;
+  int grid_mfsep;  // k_mf_adjoint_sep (0: not used by this system)
+  int grid_mfsep_fwd[3];  // k_mf_forward_sep with 1, 2, 4 sums
 };
 
 // Launchers (kernels.cu).  `st` selects solver mode (pointers and scalars from
@@ -544,6 +552,8 @@ struct MatStore {
   float *rscale = nullptr;                          // BF16 per-row scales [m]
   MfView *mfv = nullptr;                            // matrix-free view constants [V]
   float4 *mfr = nullptr, *mfs = nullptr;            // matrix-free ray table [m] (mfs: parallel)
+  float *mfz = nullptr;  // matrix-free, all views separable: A^T r of the last back projection [N]
+  float *mfy = nullptr;  // matrix-free, all views separable: row sums of the last forward [4 m]
   int V = 0, Pu = 0, Pv = 0, kind = 0;
 };
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *tmp,

@@ -28,7 +28,24 @@ def _sys(torch, geom):
     return System(geom, storage="mf")
 
 
-@pytest.mark.parametrize("name,geom", geometries(), ids=[g[0] for g in geometries()])
+def tilted_cone(n, views, det, deg=25.0):
+    """A circular cone-beam scan whose orbit is tilted by `deg` about the x
+    axis: the detector's row axis then has a y component, so the views are not
+    separable into x-y and z parts and the back projection enumerates each
+    voxel's pixels itself instead of taking the per-stack kernel's sums."""
+    g = synth.cone_geometry(n, views, det, 3.0 * n, 2.0 * n)
+    c, s = np.cos(np.radians(deg)), np.sin(np.radians(deg))
+    R = np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+    v = g.views.reshape(-1, 4, 3) @ R.T
+    return synth.Geometry(n=g.n, det_cols=g.det_cols, det_rows=g.det_rows,
+                          views=np.ascontiguousarray(v.reshape(-1, synth.VIEW_FIELDS)), kind=g.kind)
+
+
+CASES = geometries() + [("tilted_cone", tilted_cone(12, 7, 19)),
+                        ("odd_n_stacks", synth.cone_geometry(11, 6, 17, 33.0, 22.0))]
+
+
+@pytest.mark.parametrize("name,geom", CASES, ids=[g[0] for g in CASES])
 def test_forward_and_adjoint_match_the_oracle(name, geom):
     torch = cuda()
     s = _sys(torch, geom)
@@ -52,12 +69,14 @@ def test_forward_and_adjoint_match_the_oracle(name, geom):
         assert rel_l2(z.cpu().numpy(), ref) <= 1e-5, name
 
 
-def test_exact_transpose_on_a_dense_system():
+@pytest.mark.parametrize("tilt", [0.0, 25.0])
+def test_exact_transpose_on_a_dense_system(tilt):
     """Column j of the forward (x = e_j) equals row j of the back projection
-    (r = e_i gives row i of A), bit for bit; both match the oracle's A."""
+    (r = e_i gives row i of A), bit for bit; both match the oracle's A.  On
+    the untilted orbit the back projection takes the per-stack kernel's sums
+    (separable views), on the tilted one its own pixel enumeration."""
     torch = cuda()
-    from conftest import small_geometry
-    g = small_geometry(n=4, views=3, det=5)
+    g = tilted_cone(4, 3, 5, tilt)
     s = _sys(torch, g)
     Mf = np.zeros((g.m, g.N), np.float32)
     Mb = np.zeros((g.m, g.N), np.float32)
@@ -94,14 +113,14 @@ def test_phi_and_gradient_match_the_oracle():
     assert rel_l2(g.cpu().numpy(), g_ref) <= 2e-5
 
 
-@pytest.mark.parametrize("method", ["gp", "upn"])
+@pytest.mark.parametrize("method", ["gp", "gpbb", "upn"])
 def test_solve_matches_the_oracle(method):
     """x* of the matrix-free solve against the oracle's at equal eps, within
     the oracle's own spread under perturbations of b at the size of the
     float32 entry error (1e-5 relative), or 1e-3."""
     torch = cuda()
     from paper_1105_4002_gb300 import SolveOptions
-    solver = {"gp": oracle.solve_gp, "upn": oracle.solve_upn}[method]
+    solver = {"gp": oracle.solve_gp, "gpbb": oracle.solve_gpbb, "upn": oracle.solve_upn}[method]
     cfg = synth.get_config("c32")
     prob, geom, _ = oracle.problem_from_config(cfg)
     s = _sys(torch, geom)
@@ -118,6 +137,34 @@ def test_solve_matches_the_oracle(method):
             p2 = oracle.Problem(A=prob.A, b=pb, n=prob.n, alpha=prob.alpha, tau=prob.tau)
             spread = max(spread, rel_l2(solver(p2, np.zeros(prob.N), cfg.eps).x, ref.x))
         assert d <= 3 * spread, (d, spread)
+
+
+@pytest.mark.parametrize("tilt", [0.0, 25.0])
+def test_trial_sums_match_the_oracle(tilt):
+    """One projected trial step (the solvers' trial kernel, tvr_trial_sums):
+    ||A xbar - b||^2 and ||A d||^2 against the oracle's FP64 A, within the
+    float32 geometry bound of the entries (about 1e-5 of each row's sum of
+    |a_ij x_j|; A d cancels, so 1e-3 on the squared sums).  Untilted, the row sums come from the
+    per-stack forward kernel (separable views); tilted, from the walk of each
+    ray."""
+    torch = cuda()
+    g = tilted_cone(16, 9, 24, tilt)
+    s = _sys(torch, g)
+    A = oracle.system_matrix(g)
+    rng = np.random.default_rng(5)
+    p = rng.uniform(0, 1, g.N).astype(np.float32)
+    gr = rng.normal(size=g.N).astype(np.float32)
+    b = (A @ p.astype(np.float64)).astype(np.float32) * np.float32(0.5)
+    step = 0.1
+    xb = torch.empty(g.N, device="cuda")
+    sums = s.trial_sums(dev_f32(torch, p), dev_f32(torch, gr), dev_f32(torch, b), step, 1e-2,
+                        xbar=xb)
+    x64 = xb.cpu().numpy().astype(np.float64)
+    assert np.array_equal(xb.cpu().numpy(), np.maximum(p - np.float32(step) * gr, np.float32(0)))
+    r = A @ x64 - b
+    Ad = A @ (x64 - p)
+    assert sums[0] == pytest.approx(float(r @ r), rel=1e-3)
+    assert sums[1] == pytest.approx(float(Ad @ Ad), rel=1e-3)
 
 
 def test_matrix_free_rejections():
