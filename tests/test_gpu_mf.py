@@ -167,6 +167,30 @@ def test_trial_sums_match_the_oracle(tilt):
     assert sums[1] == pytest.approx(float(Ad @ Ad), rel=1e-3)
 
 
+def test_autograd_on_matrix_free_storage():
+    """phi through torch.autograd on a matrix-free system (FP32): the backward
+    gives exactly tvr_phi_and_grad's gradient, and both gradients agree with
+    the oracle within the float32 geometry bound."""
+    torch = cuda()
+    from paper_1105_4002_gb300.autograd import phi
+    cfg = synth.get_config("c32")
+    prob, geom, _ = oracle.problem_from_config(cfg)
+    s = _sys(torch, geom)
+    xn = np.random.default_rng(7).uniform(0, 1, prob.N).astype(np.float32)
+    x = torch.tensor(xn, device="cuda", requires_grad=True)
+    b = torch.tensor(prob.b, dtype=torch.float32, device="cuda", requires_grad=True)
+    f = phi(x, b, s, prob.alpha, prob.tau)
+    f.backward()
+    g = torch.empty(prob.N, device="cuda")
+    value, _, _ = s.phi_and_grad(x.detach(), b.detach(), prob.alpha, prob.tau, grad=g)
+    assert torch.equal(x.grad, g)
+    assert f.item() == pytest.approx(value, rel=1e-6)
+    f_ref, g_ref = prob.f_and_grad(xn.astype(np.float64))
+    assert abs(f.item() - f_ref) <= 2e-5 * abs(f_ref)
+    assert rel_l2(x.grad.cpu().numpy(), g_ref) <= 2e-5
+    assert rel_l2(b.grad.cpu().numpy(), -(prob.A @ xn.astype(np.float64) - prob.b)) <= 2e-5
+
+
 def test_matrix_free_rejections():
     torch = cuda()
     from paper_1105_4002_gb300._capi import TVRError as TvrError
